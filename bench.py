@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark: level-scheduled ILU-FGMRES on the 3D 7-point log-normal finite-volume matrix, 128^3.
+
+One step = one pass of the whole hot path over the workload: level analysis of L and U (Eq. 2, 3),
+HEC packing of L, U and A (Sec. 2.1, Alg. 1), solve plans, and an ILU(0)-preconditioned FGMRES(30)
+solve of A x = b to a 1e-8 relative residual (FP32 factor values, FP64 outer loop), whose every
+inner iteration runs the lower and upper sweeps (Alg. 2), SpMV and the Gram-Schmidt kernels.  The
+ILU(0) factors are computed once on the GPU before timing.  Inputs are seeded and synthetic
+(ln k ~ N(0, 2^2), b = A x_true with x_true ~ U[-1, 1]); the working set (~1 GB) is larger than L2.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "L+U sweep GB/s vs HBM peak; ILU-FGMRES time to 1e-8, FP64 vs mixed/learned"
+RESTART = 30
+RTOL = 1e-8
+
+
+def workload_name(m):
+    return ("3D 7-point FV %d^3 (n=%d), ln k ~ N(0,2^2), harmonic faces; GPU ILU(0); FP32 L/U values; "
+            "FGMRES(%d) FP64 to %.0e" % (m, m ** 3, RESTART, RTOL))
+
+
+def make_problem(m, seed=0):
+    from paper_1606_00541_gb300 import synth
+    A = synth.fv7_lognormal(m, sigma=2.0, seed=seed)
+    xt = synth.uniform_vector(m ** 3, seed + 1)
+    return A, xt
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def sweep_bytes(nnz, n, k, sv):
+    """Algorithmic bytes of one triangular sweep: values + column indices, tail row pointers, the
+    right-hand side read and the solution write (FP64), and the gather / scatter index reads."""
+    return nnz * (sv + 4) + 4 * (n + 1) + 2 * n * k * 8 + 2 * 4 * n
+
+
+# --- clocks ------------------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = open(os.devnull, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            txt, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            txt = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in txt.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --- reference arm: the CPU oracle ---------------------------------------------------------------
+
+def oracle_sample(A, b, iters, setup_levels=True):
+    """Times the oracle (serial C, one host core): ILU(0), level analysis + HEC packing of both
+    factors, and `iters` FGMRES(30) inner iterations.  Returns (setup_s, per_iter_s)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    L, U = oracle.ilu0(A)
+    t1 = time.perf_counter()
+    if setup_levels:
+        for T, up in ((L, 0), (U, 1)):
+            an = oracle.analyze(T, up)
+            oracle.hec_pack(T, 1, up, an["perm"], an["iperm"], vdt="f32")
+    t2 = time.perf_counter()
+    out = oracle.fgmres(A, b, ("ilu", L, U), m=RESTART, rtol=1e-300, max_iters=iters)
+    t3 = time.perf_counter()
+    return (t2 - t1), (t3 - t2) / max(out["iters"], 1), (t1 - t0)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    m = args.size
+    A, xt = make_problem(m)
+    import scipy.sparse as sp
+    b = sp.csr_matrix((A[2], A[1], A[0])) @ xt
+    iters_est = args.ref_iters
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(A, b, 2)
+    for _ in range(args.steps):
+        setup, per_it, fac = oracle_sample(A, b, args.ref_sample_iters)
+        vals.append(1.0 / (setup + per_it * iters_est))
+    v = statistics.median(vals)
+    line = {"metric": METRIC, "value": v, "unit": "solves/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(m), "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": "serial C oracle: level analysis + HEC packing of L and U, then %d FGMRES(30) "
+                                       "iterations timed; time to solution = setup + per-iteration time x %d "
+                                       "iterations" % (args.ref_sample_iters, iters_est)},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --- our arm --------------------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=128)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-iters", type=int, default=150, help="iteration count used to scale the oracle sample")
+    ap.add_argument("--ref-sample-iters", type=int, default=8)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1606_00541_gb300 import hec
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    devn = torch.device("cuda", local)
+
+    m = args.size
+    A, xt = make_problem(m)
+    n = m ** 3
+    Ad = [torch.as_tensor(a, device=devn) for a in A]
+    HA0 = hec.hec_from_csr(*Ad)
+    xtd = torch.as_tensor(xt, device=devn)
+    bd = hec.spmv(HA0, xtd)  # b = A x_true
+    t0 = time.perf_counter()
+    Lh, Uh = hec.ilu_factor(*Ad, k=0)
+    torch.cuda.synchronize()
+    factor_s = time.perf_counter() - t0
+    L, U = Lh.tensors(), Uh.tensors()
+    nnzL, nnzU = L[1].numel(), U[1].numel()
+
+    def step(vdt="f32", Lf=L, Uf=U, b=bd, A_=Ad):
+        s = hec.IluSolver(Lf, Uf, A=A_, vdt=vdt)
+        x, info = s.solve(b, restart=RESTART, rtol=RTOL, max_iters=5000)
+        return x, info, s
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    hec.profile_enable(True)
+    hec.profile_read(reset=True)
+    l0 = hec.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    infos = []
+    for _ in range(args.steps):
+        x, info, s = step()
+        infos.append(info)
+    e1.record()
+    torch.cuda.synchronize()
+    elapsed = e0.elapsed_time(e1) / 1000.0
+    launches = hec.launch_count() - l0
+    sweep_ms, sweep_launches = hec.profile_read(reset=True)
+    hec.profile_enable(False)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([elapsed], device=devn)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * args.steps / elapsed
+    its = infos[-1]["iterations"]
+    xr = x
+    res = bd - hec.spmv(HA0, xr)
+    relres = float(torch.linalg.norm(res) / torch.linalg.norm(bd))
+
+    # roofline of the dominant kernel (the sweep) from its live CUDA-event durations
+    hbm, src = peaks()
+    per_sweep = 0.5 * (sweep_bytes(nnzL, n, 1, 4) + sweep_bytes(nnzU, n, 1, 4))
+    avg_launch_s = (sweep_ms / 1000.0) / max(sweep_launches, 1)
+    achieved = per_sweep / avg_launch_s / 1e9
+    step_s = elapsed / args.steps
+    roofline = {"bound": "hbm", "kernel": "k_sweep<float,float,1>", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                "sweep_share_of_step": (sweep_ms / 1000.0) / elapsed,
+                "avg_sweep_us": avg_launch_s * 1e6, "bytes_per_sweep": per_sweep}
+
+    # e2e: host buffers through the public API, copies inside the timed region
+    host = [a.cpu().pin_memory() for a in (*Ad, *L, *U, bd)]
+    dev_bufs = [torch.empty_like(a, device=devn) for a in host]
+    xh = torch.empty(n, dtype=torch.float64).pin_memory()
+    h2d = sum(a.numel() * a.element_size() for a in host)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0.record()
+    for _ in range(args.steps):
+        for d_, h_ in zip(dev_bufs, host):
+            d_.copy_(h_, non_blocking=True)
+        Ae, Le, Ue, be = dev_bufs[0:3], dev_bufs[3:6], dev_bufs[6:9], dev_bufs[9]
+        xe, _, _ = step("f32", Le, Ue, be, Ae)
+        xh.copy_(xe, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1000.0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=devn)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * step_s, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": workload_name(m), "n": n, "nnz_A": int(A[0][-1]), "nnz_L": nnzL, "nnz_U": nnzU,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (about 1 GB working set)"},
+            "fgmres_iterations": its, "true_rel_residual": relres, "factor_s": factor_s,
+            "roofline": roofline,
+            "e2e": {"value": world * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": n * 8},
+            "gpu_launches": launches, "clocks": clk}
+
+    if rank == 0 and not args.no_variants:
+        line["variants"] = variants(hec, torch, Ad, L, U, bd, HA0, n, nnzL, nnzU, hbm)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            setup, per_it, fac = oracle_sample(A, bd.cpu().numpy(), args.ref_sample_iters)
+            t_est = setup + per_it * its
+            line["cpu_baseline"] = {"value": 1.0 / t_est, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                    "sample": "serial C oracle on this host: level analysis + HEC packing of L and U "
+                                              "(%.2f s), %d FGMRES(30) iterations (%.3f s each), scaled to the GPU "
+                                              "run's %d iterations; oracle ILU(0) %.2f s not counted"
+                                              % (setup, args.ref_sample_iters, per_it, its, fac)}
+        except Exception as e:  # the baseline is reported, not required
+            line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                    "sample": "failed: %s" % e}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def variants(hec, torch, Ad, L, U, bd, HA0, n, nnzL, nnzU, hbm):
+    """Time-to-1e-8 of the plain FP64 form next to the mixed forms, and L+U sweep bandwidth."""
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for vdt in ["f64", "f32", "bf16"]:
+        s = hec.IluSolver(L, U, A=Ad, vdt=vdt, max_nrhs=16)
+        s.solve(bd, restart=RESTART, rtol=RTOL, max_iters=5000)
+        torch.cuda.synchronize()
+        e0.record()
+        x, info = s.solve(bd, restart=RESTART, rtol=RTOL, max_iters=5000)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1000.0
+        sv = {"f64": 8, "f32": 4, "bf16": 2}[vdt]
+        gbs = {}
+        for k in (1, 16):
+            r = torch.randn(n, k, dtype=torch.float64, device=bd.device) if k > 1 else bd
+            for _ in range(3):
+                s.apply(r)
+            torch.cuda.synchronize()
+            reps = 10
+            e0.record()
+            for _ in range(reps):
+                s.apply(r)
+            e1.record()
+            torch.cuda.synchronize()
+            ta = e0.elapsed_time(e1) / 1000.0 / reps
+            B = sweep_bytes(nnzL, n, k, sv) + sweep_bytes(nnzU, n, k, sv)
+            gbs["nrhs%d" % k] = {"lu_us": ta * 1e6, "lu_gbs": B / ta / 1e9, "frac_hbm": B / ta / 1e9 / hbm,
+                                 "rows_per_s": n * k / ta}
+        out[vdt] = {"time_to_1e-8_s": t, "iterations": info["iterations"], "converged": info["converged"],
+                    "true_rel_residual": info["rel_residual"], "sweeps": gbs}
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,257 @@
+/*
+ * hec.h -- C ABI of libhec: level-scheduled sparse triangular solves on the HEC format, the
+ * ILU / RAS preconditioners they apply, SpMV and FGMRES, all computed by CUDA kernels on one
+ * GB300 (sm_103a).
+ *
+ * Method: Chen, Liu, Yang, "Parallel Triangular Solvers on GPU" (arXiv 1606.00541).
+ *
+ * Conventions shared by every entry point
+ *   - Indices are 0-based int32.  CSR inputs have rowptr[n+1], col[nnz], val[nnz]; every row is
+ *     sorted by ascending column (the paper assumes this, Sec. 2).
+ *   - Every array argument is a DEVICE pointer owned by the caller unless the comment says
+ *     "host".  Handles (hec_levels, hec_matrix, sptrsv_plan, ilu_precond, hec_csr) own their
+ *     internal device buffers and are released with the matching *_destroy.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default stream.  Compute
+ *     calls are asynchronous on that stream unless their comment says they synchronize.
+ *   - Dense blocks of right-hand sides are row-major n x nrhs with leading dimension ld >= nrhs
+ *     (the nrhs values of one row are contiguous).
+ *   - Every function returns a hec_status.  On failure hec_last_error() describes the cause
+ *     (thread-local, valid until the next call on the same thread).  No exception and no abort
+ *     crosses this boundary.  Device-side failures (a dependency wait that ran out of time, an
+ *     index out of bounds) are recorded in a device status word of the handle and reported by
+ *     hec_sync_status() and by fgmres_solve.
+ *   - There is no CPU fallback: when no sm_103a device is present the calls fail with
+ *     HEC_ERR_CUDA.
+ */
+#ifndef HEC_H
+#define HEC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HEC_OK = 0,
+    HEC_ERR_INVALID_ARG = 1,    /* bad size, NULL pointer, unsupported option */
+    HEC_ERR_UNSORTED = 2,       /* a CSR row not strictly ascending, or a column out of range */
+    HEC_ERR_NOT_TRIANGULAR = 3, /* an entry on the wrong side of the diagonal */
+    HEC_ERR_MISSING_DIAG = 4,   /* a row of a triangular factor without its diagonal */
+    HEC_ERR_ZERO_PIVOT = 5,     /* a zero diagonal (solve) or pivot (factorization) */
+    HEC_ERR_OOM = 6,            /* device allocation failed */
+    HEC_ERR_CUDA = 7,           /* a CUDA runtime error; see hec_last_error() */
+    HEC_ERR_TIMEOUT = 8,        /* a device-side dependency wait exceeded its time budget */
+    HEC_ERR_NOT_CONVERGED = 9,  /* FGMRES reached max_iters before rtol */
+    HEC_ERR_OUT_OF_BOUNDS = 10  /* a device-side index check failed */
+} hec_status;
+
+typedef enum { HEC_F64 = 0, HEC_F32 = 1, HEC_BF16 = 2 } hec_dtype;
+
+typedef struct hec_levels hec_levels;
+typedef struct hec_matrix hec_matrix;
+typedef struct sptrsv_plan sptrsv_plan;
+typedef struct ilu_precond ilu_precond;
+typedef struct hec_csr hec_csr;
+
+/* Message for the last failing call on this thread ("" when none). */
+const char* hec_last_error(void);
+
+/* Library version and the number of kernel launches issued by this process so far (host
+ * counter, incremented by every launch the library makes). */
+int hec_version(void);
+long long hec_launch_count(void);
+
+/* Kernel timing for measurement: while enabled, every triangular-sweep launch is bracketed by a
+ * pair of CUDA events recorded on the stream it is launched on.  hec_profile_read waits for the
+ * recorded events and returns the summed device time (ms) and the number of sweep launches
+ * since the last reset (reset != 0 clears the record).  Off by default. */
+hec_status hec_profile_enable(int on);
+hec_status hec_profile_read(double* sweep_ms, long long* sweep_launches, int reset);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Level analysis: Eq. 2 (levels), Eq. 3 (map m), Alg. 1 steps 1-2; upper factor by the       */
+/* index reversal of Sec. 2.2                                                                 */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Computes the level of every row of a triangular factor and the level-ordering map.
+ *   uplo 0: T is lower triangular; the dependencies of row i are its columns j < i.
+ *   uplo 1: T is upper triangular; it is solved as the lower problem of the reversed order
+ *           t(i) = n-1-i (the paper's t(i) = n - i with 1-based indices), so the dependencies
+ *           of row i are its columns j > i.
+ * Level (0-based; the paper's level minus one): 0 for a row without dependencies, else
+ * 1 + the largest level among its dependencies.  The diagonal is not a dependency.
+ * Map: rows are ordered by level, and within a level by ascending index of the lower problem
+ * (i for uplo 0, n-1-i for uplo 1); perm[i] is the position of original row i, iperm its
+ * inverse, level_ptr[k] the first position of level k (level_ptr[nlev] = n).
+ * The input is validated first (sorted rows, columns in range, triangular, diagonal present);
+ * a malformed factor returns UNSORTED / NOT_TRIANGULAR / MISSING_DIAG.  Synchronizes `stream`
+ * (the level count sizes the outputs).  n = 0 is allowed (nlev = 0). */
+hec_status sptrsv_analyze(int n, const int* rowptr, const int* col, int uplo, hec_levels** out,
+                          void* stream);
+
+/* Borrowed device pointers of a level analysis (valid until hec_levels_destroy):
+ * level[n], perm[n], iperm[n], level_ptr[nlev+1].  Any output pointer may be NULL. */
+hec_status hec_levels_get(const hec_levels* lv, int* n, int* nlev, int* uplo, const int** level,
+                          const int** perm, const int** iperm, const int** level_ptr);
+hec_status hec_levels_destroy(hec_levels* lv);
+
+/* ---------------------------------------------------------------------------------------- */
+/* HEC format: Sec. 2.1 (ELL slab in column-major order + CSR tail whose rows hold at least    */
+/* the diagonal), Alg. 1 steps 3-4 (reorder L to L', convert to HEC)                          */
+/* ---------------------------------------------------------------------------------------- */
+
+typedef struct {
+    int n;          /* rows */
+    int ld;         /* slab leading dimension = n rounded up to a multiple of 32 */
+    int w;          /* slab width (entries per row in the ELL part) */
+    int tri;        /* 1: triangular factor reordered by a level map; 0: general matrix */
+    int uplo;       /* for tri = 1 */
+    hec_dtype vdt;  /* value type of ell_val and tval */
+    long long tail_nnz;
+    const int* ell_col;   /* [w*ld] column of slot k of row r at k*ld + r; -1 = padding */
+    const void* ell_val;  /* [w*ld] values, same layout; padding holds +0.0 */
+    const int* tptr;      /* [n+1] tail row pointers */
+    const int* tcol;      /* [tail_nnz] */
+    const void* tval;     /* [tail_nnz] */
+} hec_matrix_info;
+
+/* Packs a CSR matrix into HEC.
+ * lv != NULL (triangular mode): the factor analysed by `lv` is reordered, L'(m(i), m(j)) =
+ *   L(i, j); each row of L' is sorted by new column; its first w off-diagonal entries go to
+ *   slab slots 0..w-1, the rest follow in the tail in ascending new column, and the diagonal
+ *   is the LAST tail entry of the row (so every tail row holds at least one entry).  Unused
+ *   slots, and every slot of rows n..ld-1, hold column -1 and value +0.0.  Columns are in the
+ *   new (level-ordered) numbering.  The factor must be the one `lv` was computed from.
+ * lv == NULL (general mode, e.g. the matrix A for SpMV): rows and columns keep their numbering
+ *   and CSR order; the first w entries of a row go to the slab, the rest to the tail, which
+ *   may then be empty for a row.
+ * ell_width: >= 0 fixes w; -1 applies the rule: the largest w such that at least
+ *   ceil(0.65 n) rows have w or more slab-eligible entries (off-diagonals in triangular mode).
+ * vdt: value storage; FP32 and BF16 values are rounded once from FP64, to nearest even
+ *   (BF16 directly from the FP64 value).
+ * Synchronizes `stream` (the width rule and the tail size are needed on the host). */
+hec_status hec_from_csr(int n, const int* rowptr, const int* col, const double* val,
+                        const hec_levels* lv, int ell_width, hec_dtype vdt, hec_matrix** out,
+                        void* stream);
+hec_status hec_matrix_get(const hec_matrix* A, hec_matrix_info* info /* host */);
+
+/* Rebuilds the CSR of the ORIGINAL matrix (original numbering, rows ascending, values widened
+ * to FP64) from HEC; lv must be the analysis used to pack it (NULL in general mode).
+ * rowptr[n+1], col[nnz], val[nnz] are caller-allocated device arrays; nnz = the number of
+ * non-padding entries.  Used for round-trip checks.  Synchronizes `stream`. */
+hec_status hec_to_csr(const hec_matrix* A, const hec_levels* lv, int* rowptr, int* col,
+                      double* val, void* stream);
+hec_status hec_matrix_destroy(hec_matrix* A);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Triangular sweeps: Alg. 2 (permute b, solve level by level, permute back) and its upper    */
+/* form by reversal (Sec. 2.2)                                                                */
+/* ---------------------------------------------------------------------------------------- */
+
+typedef struct {
+    int block_threads;      /* threads per block of the sweep kernel (0 = 256) */
+    int blocks_per_sm;      /* resident blocks per SM (0 = as many as fit) */
+    long long wait_cycles;  /* SM cycles a dependency wait may spin before HEC_ERR_TIMEOUT
+                               (0 = 2e9, about one second) */
+    int debug_unpublished_row; /* fault injection for tests: a new (level-ordered) row whose
+                                  solution is computed but never published to its dependents,
+                                  so their waits run out and the call reports HEC_ERR_TIMEOUT;
+                                  0 disables it, r + 1 selects row r */
+} hec_tune;
+
+/* A solve plan for one triangular factor: its HEC form and level analysis (both borrowed; they
+ * must outlive the plan) plus the workspace for up to max_nrhs right-hand sides
+ * (1 <= max_nrhs <= 16).  tune may be NULL for defaults. */
+hec_status sptrsv_plan_create(const hec_matrix* tri, const hec_levels* lv, int max_nrhs,
+                              const hec_tune* tune, sptrsv_plan** out);
+hec_status sptrsv_plan_destroy(sptrsv_plan* p);
+
+/* x = T^-1 b for the lower (sptrsv_lower) or upper (sptrsv_upper) factor of the plan.
+ * b and x are n x nrhs row-major FP64 (ldb, ldx >= nrhs), in the ORIGINAL row numbering; the
+ * gather b'(m(i)) = b(i) and the scatter x(i) = x'(m(i)) of Alg. 2 happen inside the sweep
+ * kernel.  Each row is computed as x'_r = (b'_r - sum_c L'_rc x'_c) / L'_rr, summing the slab
+ * slots then the tail in ascending new column; FP64 values are summed in FP64, FP32 and BF16
+ * values in FP32 (the solution is stored back as FP64).  b and x must not overlap.  The call
+ * fails with INVALID_ARG when the plan's factor has the other triangle. */
+hec_status sptrsv_lower(const sptrsv_plan* p, int nrhs, const double* b, int ldb, double* x,
+                        int ldx, void* stream);
+hec_status sptrsv_upper(const sptrsv_plan* p, int nrhs, const double* b, int ldb, double* x,
+                        int ldx, void* stream);
+
+/* Reads and clears the device status word of a plan (synchronizes `stream`).  Returns HEC_OK,
+ * HEC_ERR_TIMEOUT or HEC_ERR_OUT_OF_BOUNDS as recorded by the kernels since the last call. */
+hec_status hec_sync_status(const sptrsv_plan* p, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Preconditioners: ILU (Eq. 1: L y = r, U z = y) and Restricted Additive Schwarz with the     */
+/* subdomain factors batched block-diagonally (Sec. 3, Eq. 4)                                 */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Plain ILU: ext2glob == NULL; L and U are factors of the n x n matrix and n_glob == n.
+ * RAS: L and U are block-diagonal factors of diag(A_1, ..., A_s) over n_ext extended rows;
+ * ext2glob[n_ext] maps each extended row to its global row (a global row appears once per
+ * subdomain that contains it) and owned[n_ext] is 1 for the rows the subdomain owns (each
+ * global row owned exactly once).  ilu_apply then computes
+ * z = sum_s R0_s^T U_s^-1 L_s^-1 R_s r: gather r through ext2glob, sweep L then U, and write
+ * back only owned rows.  The plans (and arrays) are borrowed. */
+hec_status ilu_create(const sptrsv_plan* L, const sptrsv_plan* U, int n_glob, int n_ext,
+                      const int* ext2glob, const unsigned char* owned, ilu_precond** out);
+hec_status ilu_destroy(ilu_precond* M);
+
+/* z = M^-1 r; r and z are n_glob x nrhs row-major FP64 (nrhs <= the plans' max_nrhs). */
+hec_status ilu_apply(const ilu_precond* M, int nrhs, const double* r, int ldr, double* z,
+                     int ldz, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* SpMV on HEC (FP64 values) and the FGMRES outer solver                                      */
+/* ---------------------------------------------------------------------------------------- */
+
+/* y = alpha * A x + beta * y for a general-mode HEC matrix with FP64 values (beta = 0 ignores
+ * the input y).  x and y are n x nrhs row-major with ldx, ldy >= nrhs. */
+hec_status spmv(const hec_matrix* A, int nrhs, double alpha, const double* x, int ldx,
+                double beta, double* y, int ldy, void* stream);
+
+typedef struct {
+    int iterations;      /* inner iterations (largest over the right-hand sides) */
+    int restarts;
+    int converged;       /* 1 when every right-hand side reached rtol */
+    double rel_residual; /* largest true relative residual ||b - A x|| / ||b|| at exit */
+    double seconds;      /* wall time of the call, host clock */
+} hec_fgmres_info;
+
+/* Solves A x = b by right-preconditioned flexible GMRES(restart), z_j = M^-1 v_j with the ILU
+ * or RAS preconditioner M (NULL = none), FP64 throughout: SpMV, classical Gram-Schmidt with one
+ * re-orthogonalization, Givens rotations.  Each of the nrhs right-hand sides (row-major n x
+ * nrhs, nrhs <= 16) has its own Krylov space; their kernels run batched.  x holds x0 on entry
+ * (zero it for x0 = 0) and the solution on exit.  Convergence: the Arnoldi estimate
+ * |g_{j+1}| <= rtol ||b|| ends a cycle, then the true residual is checked; max_iters bounds the
+ * inner iterations.  info (host, may be NULL) receives the statistics.  Synchronizes `stream`
+ * once per inner iteration (the Hessenberg column is solved on the host).  Returns
+ * HEC_ERR_NOT_CONVERGED when max_iters is reached, HEC_ERR_TIMEOUT when a sweep's dependency
+ * wait timed out. */
+hec_status fgmres_solve(const hec_matrix* A, const ilu_precond* M, int nrhs, const double* b,
+                        int ldb, double* x, int ldx, int restart, double rtol, int max_iters,
+                        hec_fgmres_info* info /* host */, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Incomplete factorizations on the GPU (Sec. 3): ILU(0) and ILU(1) of a CSR matrix            */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Device CSR owned by the library. */
+hec_status hec_csr_get(const hec_csr* M, int* n, long long* nnz, const int** rowptr,
+                       const int** col, const double** val);
+hec_status hec_csr_destroy(hec_csr* M);
+
+/* ILU(k) for k = 0 (pattern of A) or k = 1 (pattern of A plus the fill of level 1: entries
+ * (i, j) reached by i -> q -> j with q < min(i, j) both original entries).  Each row i is
+ * eliminated IKJ-style: for the pattern columns q < i in ascending order,
+ * a_iq <- a_iq / u_qq, then a_ij <- a_ij - a_iq u_qj for pattern columns j > q of both rows.
+ * Rows run in the level order of the lower pattern with point-to-point completion waits.
+ * Outputs L (unit lower, the 1.0 diagonal stored) and U (upper with its diagonal).  A must have
+ * a nonzero diagonal in every row; ZERO_PIVOT if an eliminated pivot is zero.  Synchronizes. */
+hec_status ilu_factor(int n, const int* rowptr, const int* col, const double* val, int k,
+                      hec_csr** L, hec_csr** U, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HEC_H */

@@ -227,7 +227,7 @@ static double f32_bits_to_double(uint32_t u)
 OR_EXPORT int or_ell_width_rule(int n, const int* count)
 {
     if (n <= 0) return 0;
-    long need = (long)ceil(0.65 * (double)n);
+    long need = (65L * n + 99) / 100; /* ceil(0.65 n) in exact integer arithmetic */
     int best = 0;
     for (int w = 1;; ++w) {
         long rows = 0;

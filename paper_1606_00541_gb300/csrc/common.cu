@@ -1,0 +1,224 @@
+// Error reporting, allocation helpers, launch accounting and the device exclusive scan.
+#include <atomic>
+#include <cstdio>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace hec {
+
+static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+
+hec_status set_error(hec_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+hec_status cuda_error(cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    if (e == cudaErrorMemoryAllocation) return set_error(HEC_ERR_OOM, m);
+    return set_error(HEC_ERR_CUDA, m);
+}
+
+void clear_error() { g_last_error.clear(); }
+void count_launch(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+hec_status dmalloc(void** p, size_t bytes) {
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return cuda_error(e, "cudaMalloc");
+    }
+    return HEC_OK;
+}
+
+int num_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return sms;
+}
+
+int max_coop_blocks(const void* kernel, int threads, size_t smem) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+// ---- exclusive scan ---------------------------------------------------------------------
+// Three phases: per-tile sums, a scan of the tile sums (recursively), per-tile scan plus the
+// tile's offset.  Tiles are 256 threads x 8 items.
+namespace {
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* smem_warp, int& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int s = lane < (kScanThreads / 32) ? smem_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < (kScanThreads / 32)) smem_warp[lane] = s;
+    }
+    __syncthreads();
+    int warp_off = warp ? smem_warp[warp - 1] : 0;
+    total = smem_warp[kScanThreads / 32 - 1];
+    __syncthreads();
+    return warp_off + x - v;
+}
+
+__global__ void k_tile_sums(const int* __restrict__ in, int n, int* __restrict__ sums) {
+    __shared__ int sw[kScanThreads / 32];
+    long base = (long)blockIdx.x * kScanTile + (long)threadIdx.x * kScanItems;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        long i = base + k;
+        if (i < n) s += in[i];
+    }
+    int total;
+    block_exclusive_scan(s, sw, total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void k_tile_scan(const int* in, int n, int* out, const int* __restrict__ offs, int write_total) {
+    __shared__ int sw[kScanThreads / 32];
+    long base = (long)blockIdx.x * kScanTile + (long)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        long i = base + k;
+        v[k] = i < n ? in[i] : 0;
+        s += v[k];
+    }
+    int total;
+    int run = block_exclusive_scan(s, sw, total) + (offs ? offs[blockIdx.x] : 0);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        long i = base + k;
+        if (i < n) out[i] = run;
+        run += v[k];
+    }
+    if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) out[n] = run;
+}
+
+}  // namespace
+
+hec_status exclusive_scan_i32(const int* in, int* out, int n, bool write_total, cudaStream_t s) {
+    if (n <= 0) {
+        if (write_total) {
+            HEC_CUDA(cudaMemsetAsync(out, 0, sizeof(int), s));
+        }
+        return HEC_OK;
+    }
+    int tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 1) {
+        k_tile_scan<<<1, kScanThreads, 0, s>>>(in, n, out, nullptr, write_total ? 1 : 0);
+        HEC_LAUNCHED();
+        return HEC_OK;
+    }
+    int* sums = nullptr;
+    HEC_CHECK(dalloc(&sums, (size_t)tiles + 1));
+    k_tile_sums<<<tiles, kScanThreads, 0, s>>>(in, n, sums);
+    count_launch();
+    hec_status st = exclusive_scan_i32(sums, sums, tiles, false, s);
+    if (st == HEC_OK) {
+        k_tile_scan<<<tiles, kScanThreads, 0, s>>>(in, n, out, sums, write_total ? 1 : 0);
+        count_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) st = cuda_error(e, "scan");
+    }
+    // sums must outlive the kernels that read it: free after the stream drains this work
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(sums);
+    if (st == HEC_OK && e != cudaSuccess) st = cuda_error(e, "scan sync");
+    return st;
+}
+
+}  // namespace hec
+
+// ---- sweep timing (measurement only) ------------------------------------------------------
+namespace hec {
+namespace {
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_used, g_prof_free;
+}  // namespace
+
+bool profiling() { return g_prof_on; }
+
+void profile_begin(cudaStream_t s, void** token) {
+    *token = nullptr;
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    std::pair<cudaEvent_t, cudaEvent_t> ev;
+    if (!g_prof_free.empty()) {
+        ev = g_prof_free.back();
+        g_prof_free.pop_back();
+    } else {
+        if (cudaEventCreate(&ev.first) != cudaSuccess || cudaEventCreate(&ev.second) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+    }
+    cudaEventRecord(ev.first, s);
+    g_prof_used.push_back(ev);
+    *token = (void*)(g_prof_used.size());
+}
+
+void profile_end(cudaStream_t s, void* token) {
+    if (!token) return;
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    size_t idx = (size_t)token - 1;
+    if (idx < g_prof_used.size()) cudaEventRecord(g_prof_used[idx].second, s);
+}
+}  // namespace hec
+
+HEC_API hec_status hec_profile_enable(int on) {
+    hec::g_prof_on = on != 0;
+    return HEC_OK;
+}
+
+HEC_API hec_status hec_profile_read(double* sweep_ms, long long* launches, int reset) {
+    std::lock_guard<std::mutex> g(hec::g_prof_mu);
+    double tot = 0.0;
+    for (auto& ev : hec::g_prof_used) {
+        cudaEventSynchronize(ev.second);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) tot += ms;
+        else cudaGetLastError();
+    }
+    if (sweep_ms) *sweep_ms = tot;
+    if (launches) *launches = (long long)hec::g_prof_used.size();
+    if (reset) {
+        for (auto& ev : hec::g_prof_used) hec::g_prof_free.push_back(ev);
+        hec::g_prof_used.clear();
+    }
+    return HEC_OK;
+}
+
+HEC_API const char* hec_last_error(void) { return hec::g_last_error.c_str(); }
+HEC_API int hec_version(void) { return 1; }
+HEC_API long long hec_launch_count(void) { return hec::g_launches.load(); }

@@ -1,0 +1,120 @@
+// Internal declarations shared by the libhec translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/hec.h"
+
+#define HEC_API extern "C" __attribute__((visibility("default")))
+
+namespace hec {
+
+// ---- errors ------------------------------------------------------------------------------
+hec_status set_error(hec_status s, const std::string& msg);
+hec_status cuda_error(cudaError_t e, const char* what);
+void clear_error();
+void count_launch(long long k = 1);
+
+#define HEC_CUDA(call)                                                   \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return ::hec::cuda_error(e_, #call);      \
+    } while (0)
+
+#define HEC_CHECK(st)                          \
+    do {                                       \
+        hec_status s_ = (st);                  \
+        if (s_ != HEC_OK) return s_;           \
+    } while (0)
+
+#define HEC_LAUNCHED()                                                    \
+    do {                                                                  \
+        ::hec::count_launch();                                            \
+        cudaError_t e_ = cudaGetLastError();                              \
+        if (e_ != cudaSuccess) return ::hec::cuda_error(e_, "kernel launch"); \
+    } while (0)
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// device allocation that reports OOM as a status
+hec_status dmalloc(void** p, size_t bytes);
+template <typename T>
+hec_status dalloc(T** p, size_t count) { return dmalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16); }
+
+int num_sms();
+// measurement hooks around sweep launches (no-ops unless hec_profile_enable(1))
+void profile_begin(cudaStream_t s, void** token);
+void profile_end(cudaStream_t s, void* token);
+int max_coop_blocks(const void* kernel, int threads, size_t smem);  // resident blocks per SM
+
+// ---- device status word codes -------------------------------------------------------------
+// Written with atomicCAS(status, 0, code) so the first failure sticks.
+enum : int { DEV_OK = 0, DEV_TIMEOUT = HEC_ERR_TIMEOUT, DEV_OOB = HEC_ERR_OUT_OF_BOUNDS,
+             DEV_ZERO_PIVOT = HEC_ERR_ZERO_PIVOT };
+
+// ---- exclusive scan of int32 (device) -----------------------------------------------------
+// out[i] = sum_{j<i} in[i]; out[n] = total when out has n+1 entries (total_out selects).
+// in and out may alias.  Uses a workspace from the scan module's own cache.
+hec_status exclusive_scan_i32(const int* in, int* out, int n, bool write_total, cudaStream_t s);
+
+// ---- opaque handle definitions ------------------------------------------------------------
+}  // namespace hec
+
+struct hec_levels {
+    int n = 0, nlev = 0, uplo = 0;
+    int* level = nullptr;      // [n]
+    int* perm = nullptr;       // [n]
+    int* iperm = nullptr;      // [n]
+    int* level_ptr = nullptr;  // [nlev+1]
+};
+
+struct hec_matrix {
+    int n = 0, ld = 0, w = 0, tri = 0, uplo = 0;
+    hec_dtype vdt = HEC_F64;
+    long long tail_nnz = 0;
+    int* ell_col = nullptr;
+    void* ell_val = nullptr;
+    int* tptr = nullptr;
+    int* tcol = nullptr;
+    void* tval = nullptr;
+    const hec_levels* lv = nullptr;  // analysis used to pack (borrowed), NULL in general mode
+};
+
+struct sptrsv_plan {
+    const hec_matrix* T = nullptr;
+    const hec_levels* lv = nullptr;
+    int max_nrhs = 1;
+    int threads = 256, blocks = 0;
+    long long wait_cycles = 2000000000LL;
+    int skip_row = -1;         // fault injection: row never published (tests only)
+    void* xp = nullptr;        // internal solution in level order, n * max_nrhs of the work type
+    int* status = nullptr;     // device status word
+};
+
+struct ilu_precond {
+    const sptrsv_plan* L = nullptr;
+    const sptrsv_plan* U = nullptr;
+    int n_glob = 0, n_ext = 0;
+    int* l_gather = nullptr;   // [n_ext] lower sweep: new row -> row of r to read
+    int* l_scatter = nullptr;  // [n_ext] lower sweep: new row -> row of the intermediate y (in U order)
+    int* u_scatter = nullptr;  // [n_ext] upper sweep: new row -> row of z to write, -1 = not owned
+    double* y = nullptr;       // [n_ext * max_nrhs] intermediate, already in the upper factor's order
+    int max_nrhs = 1;
+};
+
+struct hec_csr {
+    int n = 0;
+    long long nnz = 0;
+    int* rowptr = nullptr;
+    int* col = nullptr;
+    double* val = nullptr;
+};
+
+namespace hec {
+// sweep launcher shared by sptrsv_* and ilu_apply: gather[r] is the row of b feeding new row r
+// (NULL = identity), scatter[r] the row of x receiving it (NULL = identity, -1 = skip).
+hec_status sweep(const sptrsv_plan* p, int nrhs, const double* b, int ldb, const int* gather, double* x,
+                 int ldx, const int* scatter, cudaStream_t s);
+}  // namespace hec

@@ -1,0 +1,333 @@
+// Level-ordered triangular sweeps on HEC (Alg. 2; upper factor by the reversal of Sec. 2.2)
+// and the ILU / RAS preconditioner apply built on them (Eq. 1, Eq. 4).
+//
+// GB300 design.  The paper launches one kernel per level with one thread per row.  On GB300 a
+// kernel boundary (or a grid-wide barrier) costs about a microsecond, which for the 382 levels
+// of a 128^3 ILU(0) factor is far more than the time to stream the factor from HBM.  Here one
+// cooperative persistent launch solves every level: rows are processed in level order (the
+// order of L'), chunk c of rows going to warp c mod W, and each row waits point to point only
+// for the rows it actually depends on by polling their solution words (see sync.cuh).  Every
+// dependency of row r lies in an earlier chunk, so with all warps resident the earliest
+// unfinished chunk can always proceed.  The HEC slab is read column-major, so the consecutive
+// rows of a warp read consecutive addresses; the gather of b (b'(m(i)) = b(i)) and the scatter
+// of x (x(i) = x'(m(i))) of Alg. 2 are fused into the row's first load and last store.
+//
+// Multiple right-hand sides: lane = (row of the warp's chunk, right-hand side), with the
+// right-hand sides of a row interleaved, so one slab entry serves up to 16 solves.
+#include <algorithm>
+#include <mutex>
+#include <unordered_map>
+
+#include "internal.cuh"
+#include "sync.cuh"
+
+namespace hec {
+namespace {
+
+struct SweepParams {
+    int n, ld, w, K;
+    const int* __restrict__ ell_col;
+    const void* __restrict__ ell_val;
+    const int* __restrict__ tptr;
+    const int* __restrict__ tcol;
+    const void* __restrict__ tval;
+    const double* __restrict__ b;
+    int ldb;
+    const int* __restrict__ gather;
+    double* __restrict__ x;
+    int ldx;
+    const int* __restrict__ scatter;
+    void* xp;
+    int* status;
+    long long budget;
+    int skip_row;
+};
+
+template <typename XT> struct Acc { typedef float T; };
+template <> struct Acc<double> { typedef double T; };
+
+template <typename VT, typename AT> __device__ __forceinline__ AT ldv(const VT* p) { return (AT)__ldg(p); }
+template <> __device__ __forceinline__ float ldv<__nv_bfloat16, float>(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldg(p));
+}
+
+__device__ __forceinline__ double wait_x(const double* p, int* st, long long b) { return wait_f64(p, st, b); }
+__device__ __forceinline__ float wait_x(const float* p, int* st, long long b) { return wait_f32(p, st, b); }
+__device__ __forceinline__ void publish_x(double* p, double v) { publish_f64(p, v); }
+__device__ __forceinline__ void publish_x(float* p, float v) { publish_f32(p, v); }
+
+template <typename VT, typename XT, int KP>
+__global__ void __launch_bounds__(256) k_sweep(SweepParams p) {
+    typedef typename Acc<XT>::T AT;
+    constexpr int RPW = 32 / KP;  // rows per warp step
+    const int lane = threadIdx.x & 31;
+    const int rsub = lane / KP, q = lane % KP;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int nchunks = (p.n + RPW - 1) / RPW;
+    const VT* __restrict__ ev = (const VT*)p.ell_val;
+    const VT* __restrict__ tv = (const VT*)p.tval;
+    XT* xp = (XT*)p.xp;
+    const int K = p.K;
+    for (int c = gw; c < nchunks; c += nw) {
+        const int r = c * RPW + rsub;
+        if (r >= p.n || q >= K) continue;
+        const int gr = p.gather ? __ldg(p.gather + r) : r;
+        AT acc = (AT)__ldg(p.b + (long)gr * p.ldb + q);
+        // slab entries of row r (padding, column -1, only after the row's entries)
+        for (int k = 0; k < p.w; ++k) {
+            const long s = (long)k * p.ld + r;
+            const int cc = __ldg(p.ell_col + s);
+            if (cc < 0) break;
+            const AT v = ldv<VT, AT>(ev + s);
+            const AT xc = (AT)wait_x(xp + (long)cc * K + q, p.status, p.budget);
+            acc = fma(-v, xc, acc);
+        }
+        // tail: overflow off-diagonals, then the diagonal
+        const int t0 = __ldg(p.tptr + r), t1 = __ldg(p.tptr + r + 1) - 1;
+        for (int t = t0; t < t1; ++t) {
+            const int cc = __ldg(p.tcol + t);
+            const AT v = ldv<VT, AT>(tv + t);
+            const AT xc = (AT)wait_x(xp + (long)cc * K + q, p.status, p.budget);
+            acc = fma(-v, xc, acc);
+        }
+        const AT xr = acc / ldv<VT, AT>(tv + t1);
+        if (r != p.skip_row) publish_x(xp + (long)r * K + q, (XT)xr);
+        const int sr = p.scatter ? __ldg(p.scatter + r) : r;
+        if (sr >= 0) p.x[(long)sr * p.ldx + q] = (double)xr;
+    }
+}
+
+template <typename XT>
+__global__ void k_fill_sentinel(XT* xp, long count) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long st = (long)gridDim.x * blockDim.x;
+    for (; i < count; i += st) {
+        if (sizeof(XT) == 8) ((unsigned long long*)xp)[i] = kSent64;
+        else ((unsigned int*)xp)[i] = kSent32;
+    }
+}
+
+std::mutex g_occ_mu;
+std::unordered_map<const void*, int> g_occ;
+
+int occupancy(const void* k, int threads) {
+    std::lock_guard<std::mutex> g(g_occ_mu);
+    auto it = g_occ.find(k);
+    if (it != g_occ.end()) return it->second;
+    int nb = max_coop_blocks(k, threads, 0);
+    g_occ[k] = nb;
+    return nb;
+}
+
+template <typename VT, typename XT, int KP>
+hec_status launch_sweep(const sptrsv_plan* pl, SweepParams& sp, cudaStream_t s) {
+    const void* k = (const void*)k_sweep<VT, XT, KP>;
+    const int threads = pl->threads;
+    int per_sm = occupancy(k, threads);
+    if (per_sm <= 0) return set_error(HEC_ERR_CUDA, "sweep kernel cannot be resident");
+    if (pl->blocks > 0) per_sm = std::min(per_sm, pl->blocks);
+    constexpr int RPW = 32 / KP;
+    long nchunks = (sp.n + RPW - 1) / RPW;
+    long want = (nchunks + threads / 32 - 1) / (threads / 32);
+    int blocks = (int)std::max(1L, std::min((long)per_sm * num_sms(), want));
+    long count = (long)sp.n * sp.K;
+    int fb = (int)std::min(4096L, std::max(1L, (count + 255) / 256));
+    k_fill_sentinel<XT><<<fb, 256, 0, s>>>((XT*)sp.xp, count);
+    HEC_LAUNCHED();
+    void* args[] = {&sp};
+    void* tok = nullptr;
+    profile_begin(s, &tok);
+    HEC_CUDA(cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(threads), args, 0, s));
+    profile_end(s, tok);
+    count_launch();
+    return HEC_OK;
+}
+
+template <typename VT, typename XT>
+hec_status dispatch_k(const sptrsv_plan* pl, SweepParams& sp, cudaStream_t s) {
+    if (sp.K <= 1) return launch_sweep<VT, XT, 1>(pl, sp, s);
+    if (sp.K <= 2) return launch_sweep<VT, XT, 2>(pl, sp, s);
+    if (sp.K <= 4) return launch_sweep<VT, XT, 4>(pl, sp, s);
+    if (sp.K <= 8) return launch_sweep<VT, XT, 8>(pl, sp, s);
+    return launch_sweep<VT, XT, 16>(pl, sp, s);
+}
+
+size_t work_size(hec_dtype d) { return d == HEC_F64 ? 8 : 4; }
+
+}  // namespace
+
+hec_status sweep(const sptrsv_plan* pl, int nrhs, const double* b, int ldb, const int* gather, double* x, int ldx,
+                 const int* scatter, cudaStream_t s) {
+    const hec_matrix* T = pl->T;
+    if (T->n == 0) return HEC_OK;
+    SweepParams sp;
+    sp.n = T->n;
+    sp.ld = T->ld;
+    sp.w = T->w;
+    sp.K = nrhs;
+    sp.ell_col = T->ell_col;
+    sp.ell_val = T->ell_val;
+    sp.tptr = T->tptr;
+    sp.tcol = T->tcol;
+    sp.tval = T->tval;
+    sp.b = b;
+    sp.ldb = ldb;
+    sp.gather = gather;
+    sp.x = x;
+    sp.ldx = ldx;
+    sp.scatter = scatter;
+    sp.xp = pl->xp;
+    sp.status = pl->status;
+    sp.budget = pl->wait_cycles;
+    sp.skip_row = pl->skip_row;
+    switch (T->vdt) {
+        case HEC_F64: return dispatch_k<double, double>(pl, sp, s);
+        case HEC_F32: return dispatch_k<float, float>(pl, sp, s);
+        default: return dispatch_k<__nv_bfloat16, float>(pl, sp, s);
+    }
+}
+
+namespace {
+__global__ void k_ilu_maps(int n, const int* __restrict__ iperm_l, const int* __restrict__ perm_u,
+                           const int* __restrict__ iperm_u, const int* __restrict__ ext2glob,
+                           const unsigned char* __restrict__ owned, int* lg, int* ls, int* us) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int il = iperm_l[r];
+    lg[r] = ext2glob ? ext2glob[il] : il;  // lower sweep reads r at the global row of its extended row
+    ls[r] = perm_u[il];                    // and writes y straight into the upper factor's order
+    int iu = iperm_u[r];
+    us[r] = ext2glob ? (owned[iu] ? ext2glob[iu] : -1) : iu;  // upper sweep writes owned rows only
+}
+}  // namespace
+
+void free_plan(sptrsv_plan* p) {
+    if (!p) return;
+    cudaFree(p->xp);
+    cudaFree(p->status);
+    delete p;
+}
+
+}  // namespace hec
+
+using namespace hec;
+
+HEC_API hec_status sptrsv_plan_create(const hec_matrix* tri, const hec_levels* lv, int max_nrhs, const hec_tune* tune,
+                                      sptrsv_plan** out) {
+    clear_error();
+    if (!out || !tri || !lv || !tri->tri || tri->lv != lv || max_nrhs < 1 || max_nrhs > 16)
+        return set_error(HEC_ERR_INVALID_ARG,
+                         "sptrsv_plan_create: need a triangular HEC matrix, the analysis it was packed with, 1 <= max_nrhs <= 16");
+    *out = nullptr;
+    sptrsv_plan* p = new sptrsv_plan();
+    p->T = tri;
+    p->lv = lv;
+    p->max_nrhs = max_nrhs;
+    if (tune) {
+        if (tune->block_threads) p->threads = tune->block_threads;
+        if (tune->blocks_per_sm) p->blocks = tune->blocks_per_sm;
+        if (tune->wait_cycles) p->wait_cycles = tune->wait_cycles;
+        if (tune->debug_unpublished_row > 0) p->skip_row = tune->debug_unpublished_row - 1;
+    }
+    if (p->threads % 32 || p->threads < 32 || p->threads > 256) {
+        delete p;
+        return set_error(HEC_ERR_INVALID_ARG, "sptrsv_plan_create: block_threads must be a multiple of 32 in [32, 256]");
+    }
+    hec_status st = dmalloc(&p->xp, work_size(tri->vdt) * (size_t)tri->n * max_nrhs + 16);
+    if (st == HEC_OK) st = dalloc(&p->status, 1);
+    if (st == HEC_OK && cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) st = cuda_error(cudaGetLastError(), "memset");
+    if (st != HEC_OK) { free_plan(p); return st; }
+    *out = p;
+    return HEC_OK;
+}
+
+HEC_API hec_status sptrsv_plan_destroy(sptrsv_plan* p) {
+    free_plan(p);
+    return HEC_OK;
+}
+
+static hec_status sweep_api(const sptrsv_plan* p, int uplo, int nrhs, const double* b, int ldb, double* x, int ldx,
+                            void* stream) {
+    clear_error();
+    if (!p || p->T->uplo != uplo || nrhs < 1 || nrhs > p->max_nrhs || ldb < nrhs || ldx < nrhs ||
+        (p->T->n > 0 && (!b || !x)))
+        return set_error(HEC_ERR_INVALID_ARG, uplo ? "sptrsv_upper: bad argument" : "sptrsv_lower: bad argument");
+    return sweep(p, nrhs, b, ldb, p->lv->iperm, x, ldx, p->lv->iperm, S(stream));
+}
+
+HEC_API hec_status sptrsv_lower(const sptrsv_plan* p, int nrhs, const double* b, int ldb, double* x, int ldx,
+                                void* stream) {
+    return sweep_api(p, 0, nrhs, b, ldb, x, ldx, stream);
+}
+
+HEC_API hec_status sptrsv_upper(const sptrsv_plan* p, int nrhs, const double* b, int ldb, double* x, int ldx,
+                                void* stream) {
+    return sweep_api(p, 1, nrhs, b, ldb, x, ldx, stream);
+}
+
+HEC_API hec_status hec_sync_status(const sptrsv_plan* p, void* stream) {
+    if (!p) return set_error(HEC_ERR_INVALID_ARG, "hec_sync_status: NULL");
+    int h = 0;
+    cudaStream_t s = S(stream);
+    HEC_CUDA(cudaMemcpyAsync(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HEC_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), s));
+    HEC_CUDA(cudaStreamSynchronize(s));
+    if (h == 0) return HEC_OK;
+    return set_error((hec_status)h, h == HEC_ERR_TIMEOUT ? "a dependency wait timed out" : "device-side check failed");
+}
+
+HEC_API hec_status ilu_create(const sptrsv_plan* L, const sptrsv_plan* U, int n_glob, int n_ext, const int* ext2glob,
+                              const unsigned char* owned, ilu_precond** out) {
+    clear_error();
+    if (!out || !L || !U || L->T->uplo != 0 || U->T->uplo != 1 || L->T->n != n_ext || U->T->n != n_ext || n_glob < 0 ||
+        (!ext2glob && n_glob != n_ext) || (ext2glob && !owned))
+        return set_error(HEC_ERR_INVALID_ARG, "ilu_create: bad argument");
+    *out = nullptr;
+    ilu_precond* M = new ilu_precond();
+    M->L = L;
+    M->U = U;
+    M->n_glob = n_glob;
+    M->n_ext = n_ext;
+    M->max_nrhs = std::min(L->max_nrhs, U->max_nrhs);
+    hec_status st = HEC_OK;
+    if ((st = dalloc(&M->l_gather, (size_t)n_ext)) || (st = dalloc(&M->l_scatter, (size_t)n_ext)) ||
+        (st = dalloc(&M->u_scatter, (size_t)n_ext)) || (st = dalloc(&M->y, (size_t)n_ext * M->max_nrhs))) {
+        ilu_destroy(M);
+        return st;
+    }
+    if (n_ext > 0) {
+        k_ilu_maps<<<(n_ext + 255) / 256, 256>>>(n_ext, L->lv->iperm, U->lv->perm, U->lv->iperm, ext2glob, owned,
+                                                  M->l_gather, M->l_scatter, M->u_scatter);
+        count_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            ilu_destroy(M);
+            return cuda_error(e, "ilu_create");
+        }
+    }
+    *out = M;
+    return HEC_OK;
+}
+
+HEC_API hec_status ilu_destroy(ilu_precond* M) {
+    if (!M) return HEC_OK;
+    cudaFree(M->l_gather);
+    cudaFree(M->l_scatter);
+    cudaFree(M->u_scatter);
+    cudaFree(M->y);
+    delete M;
+    return HEC_OK;
+}
+
+HEC_API hec_status ilu_apply(const ilu_precond* M, int nrhs, const double* r, int ldr, double* z, int ldz, void* stream) {
+    clear_error();
+    if (!M || nrhs < 1 || nrhs > M->max_nrhs || ldr < nrhs || ldz < nrhs || (M->n_glob > 0 && (!r || !z)))
+        return set_error(HEC_ERR_INVALID_ARG, "ilu_apply: bad argument");
+    cudaStream_t s = S(stream);
+    // L y = r: gather r, write y already permuted into the upper factor's level order
+    HEC_CHECK(sweep(M->L, nrhs, r, ldr, M->l_gather, M->y, nrhs, M->l_scatter, s));
+    // U z = y: y is read in order, z is written back (owned rows only for RAS)
+    return sweep(M->U, nrhs, M->y, nrhs, nullptr, z, ldz, M->u_scatter, s);
+}

@@ -1,0 +1,383 @@
+"""Python binding of libhec (argument marshalling only: every step runs in the CUDA library).
+
+Names follow the C ABI in include/hec.h.  Device arrays are torch CUDA tensors (int32 indices,
+float64 values); streams default to torch's current stream.  Importing this module loads
+libhec.so and raises ImportError when it is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhec.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libhec.so is not built (run paper_1606_00541_gb300.build.build() or __graft_entry__.build())")
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, INVALID_ARG, UNSORTED, NOT_TRIANGULAR, MISSING_DIAG, ZERO_PIVOT, OOM, CUDA, TIMEOUT, NOT_CONVERGED, OUT_OF_BOUNDS = range(11)
+STATUS_NAMES = ["OK", "INVALID_ARG", "UNSORTED", "NOT_TRIANGULAR", "MISSING_DIAG", "ZERO_PIVOT", "OOM", "CUDA",
+                "TIMEOUT", "NOT_CONVERGED", "OUT_OF_BOUNDS"]
+DTYPES = {"f64": 0, "f32": 1, "bf16": 2}
+
+
+class HecError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.hec_last_error().decode()
+        super().__init__("%s: %s (%s)" % (where, STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status, msg))
+
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+_ll = ctypes.c_longlong
+
+
+class HecMatrixInfo(ctypes.Structure):
+    _fields_ = [("n", _i), ("ld", _i), ("w", _i), ("tri", _i), ("uplo", _i), ("vdt", _i), ("tail_nnz", _ll),
+                ("ell_col", _vp), ("ell_val", _vp), ("tptr", _vp), ("tcol", _vp), ("tval", _vp)]
+
+
+class HecTune(ctypes.Structure):
+    _fields_ = [("block_threads", _i), ("blocks_per_sm", _i), ("wait_cycles", _ll), ("debug_unpublished_row", _i)]
+
+
+class HecFgmresInfo(ctypes.Structure):
+    _fields_ = [("iterations", _i), ("restarts", _i), ("converged", _i), ("rel_residual", _d), ("seconds", _d)]
+
+
+def _sig(name, *args):
+    f = getattr(_lib, name)
+    f.restype = _i
+    f.argtypes = list(args)
+    return f
+
+
+_lib.hec_last_error.restype = ctypes.c_char_p
+_lib.hec_version.restype = _i
+_lib.hec_launch_count.restype = _ll
+_sptrsv_analyze = _sig("sptrsv_analyze", _i, _vp, _vp, _i, ctypes.POINTER(_vp), _vp)
+_hec_levels_get = _sig("hec_levels_get", _vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                       ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp))
+_hec_levels_destroy = _sig("hec_levels_destroy", _vp)
+_hec_from_csr = _sig("hec_from_csr", _i, _vp, _vp, _vp, _vp, _i, _i, ctypes.POINTER(_vp), _vp)
+_hec_matrix_get = _sig("hec_matrix_get", _vp, ctypes.POINTER(HecMatrixInfo))
+_hec_to_csr = _sig("hec_to_csr", _vp, _vp, _vp, _vp, _vp, _vp)
+_hec_matrix_destroy = _sig("hec_matrix_destroy", _vp)
+_sptrsv_plan_create = _sig("sptrsv_plan_create", _vp, _vp, _i, ctypes.POINTER(HecTune), ctypes.POINTER(_vp))
+_sptrsv_plan_destroy = _sig("sptrsv_plan_destroy", _vp)
+_sptrsv_lower = _sig("sptrsv_lower", _vp, _i, _vp, _i, _vp, _i, _vp)
+_sptrsv_upper = _sig("sptrsv_upper", _vp, _i, _vp, _i, _vp, _i, _vp)
+_hec_sync_status = _sig("hec_sync_status", _vp, _vp)
+_ilu_create = _sig("ilu_create", _vp, _vp, _i, _i, _vp, _vp, ctypes.POINTER(_vp))
+_ilu_destroy = _sig("ilu_destroy", _vp)
+_ilu_apply = _sig("ilu_apply", _vp, _i, _vp, _i, _vp, _i, _vp)
+_spmv = _sig("spmv", _vp, _i, _d, _vp, _i, _d, _vp, _i, _vp)
+_fgmres_solve = _sig("fgmres_solve", _vp, _vp, _i, _vp, _i, _vp, _i, _i, _d, _i, ctypes.POINTER(HecFgmresInfo), _vp)
+_hec_csr_get = _sig("hec_csr_get", _vp, ctypes.POINTER(_i), ctypes.POINTER(_ll), ctypes.POINTER(_vp),
+                    ctypes.POINTER(_vp), ctypes.POINTER(_vp))
+_hec_csr_destroy = _sig("hec_csr_destroy", _vp)
+_ilu_factor = _sig("ilu_factor", _i, _vp, _vp, _vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp)
+
+
+def _check(st, where):
+    if st != OK:
+        raise HecError(st, where)
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _ld(t, nrhs):
+    return nrhs if t.dim() == 1 else t.stride(0)
+
+
+def _nrhs(t):
+    return 1 if t.dim() == 1 else t.shape[1]
+
+
+_hec_profile_enable = _sig("hec_profile_enable", _i)
+_hec_profile_read = _sig("hec_profile_read", ctypes.POINTER(_d), ctypes.POINTER(_ll), _i)
+
+
+def profile_enable(on=True):
+    _check(_hec_profile_enable(1 if on else 0), "hec_profile_enable")
+
+
+def profile_read(reset=True):
+    """(summed device ms, launches) of the sweep kernels recorded since the last reset."""
+    ms, n = _d(), _ll()
+    _check(_hec_profile_read(ctypes.byref(ms), ctypes.byref(n), 1 if reset else 0), "hec_profile_read")
+    return ms.value, n.value
+
+
+def version():
+    return _lib.hec_version()
+
+
+def launch_count():
+    """Kernel launches the library has issued in this process."""
+    return _lib.hec_launch_count()
+
+
+def library_path():
+    return LIB_PATH
+
+
+class _DevArray:
+    """Borrowed device array exposed through __cuda_array_interface__ (for torch.as_tensor)."""
+
+    def __init__(self, ptr, n, typestr, owner):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr or 0, False), "version": 3,
+                                         "strides": None}
+
+
+def _view(ptr, n, dtype, owner):
+    typestr = {torch.int32: "<i4", torch.float64: "<f8", torch.float32: "<f4", torch.int16: "<i2"}[dtype]
+    if n == 0:
+        return torch.zeros(0, dtype=dtype, device="cuda")
+    return torch.as_tensor(_DevArray(ptr, n, typestr, owner), device="cuda")
+
+
+class _Handle:
+    _destroy = None
+
+    def __init__(self, h, keep=()):
+        self.h = h
+        self._keep = keep  # objects this handle borrows from
+
+    def close(self):
+        if self.h:
+            type(self)._destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        return self.h
+
+
+class Levels(_Handle):
+    _destroy = staticmethod(_hec_levels_destroy)
+
+    def _get(self):
+        n, nlev, uplo = _i(), _i(), _i()
+        p = [_vp() for _ in range(4)]
+        _check(_hec_levels_get(self.h, ctypes.byref(n), ctypes.byref(nlev), ctypes.byref(uplo), *[ctypes.byref(x) for x in p]),
+               "hec_levels_get")
+        return n.value, nlev.value, uplo.value, [x.value for x in p]
+
+    @property
+    def n(self):
+        return self._get()[0]
+
+    @property
+    def nlev(self):
+        return self._get()[1]
+
+    @property
+    def uplo(self):
+        return self._get()[2]
+
+    def arrays(self):
+        """Copies of (level, perm, iperm, level_ptr) as torch int32 CUDA tensors."""
+        n, nlev, _, (lev, perm, iperm, lp) = self._get()
+        return (_view(lev, n, torch.int32, self).clone(), _view(perm, n, torch.int32, self).clone(),
+                _view(iperm, n, torch.int32, self).clone(), _view(lp, nlev + 1, torch.int32, self).clone())
+
+
+class Matrix(_Handle):
+    _destroy = staticmethod(_hec_matrix_destroy)
+
+    def info(self):
+        inf = HecMatrixInfo()
+        _check(_hec_matrix_get(self.h, ctypes.byref(inf)), "hec_matrix_get")
+        return inf
+
+    def arrays(self):
+        """Copies of the HEC arrays: dict(n, ld, w, ell_col, ell_val, tptr, tcol, tval); f32 and bf16
+        values are returned as their raw int32 / int16 bit patterns."""
+        inf = self.info()
+        vdt = inf.vdt
+        vt = {0: torch.float64, 1: torch.int32, 2: torch.int16}[vdt]
+        wl = inf.w * inf.ld
+        return dict(n=inf.n, ld=inf.ld, w=inf.w, tri=inf.tri, uplo=inf.uplo, vdt=["f64", "f32", "bf16"][vdt],
+                    ell_col=_view(inf.ell_col, wl, torch.int32, self).clone(),
+                    ell_val=_view(inf.ell_val, wl, vt, self).clone(),
+                    tptr=_view(inf.tptr, inf.n + 1, torch.int32, self).clone(),
+                    tcol=_view(inf.tcol, inf.tail_nnz, torch.int32, self).clone(),
+                    tval=_view(inf.tval, inf.tail_nnz, vt, self).clone())
+
+
+class Plan(_Handle):
+    _destroy = staticmethod(_sptrsv_plan_destroy)
+
+
+class Precond(_Handle):
+    _destroy = staticmethod(_ilu_destroy)
+
+
+class Csr(_Handle):
+    _destroy = staticmethod(_hec_csr_destroy)
+
+    def tensors(self):
+        n, nnz = _i(), _ll()
+        p = [_vp() for _ in range(3)]
+        _check(_hec_csr_get(self.h, ctypes.byref(n), ctypes.byref(nnz), *[ctypes.byref(x) for x in p]), "hec_csr_get")
+        return (_view(p[0].value, n.value + 1, torch.int32, self).clone(),
+                _view(p[1].value, nnz.value, torch.int32, self).clone(),
+                _view(p[2].value, nnz.value, torch.float64, self).clone())
+
+
+# --- entry points -----------------------------------------------------------------------------
+
+def sptrsv_analyze(rowptr, col, uplo, stream=None):
+    n = rowptr.numel() - 1
+    out = _vp()
+    _check(_sptrsv_analyze(n, _ptr(rowptr), _ptr(col), int(uplo), ctypes.byref(out), _stream(stream)), "sptrsv_analyze")
+    return Levels(out.value)
+
+
+def hec_from_csr(rowptr, col, val, levels=None, ell_width=-1, vdt="f64", stream=None):
+    n = rowptr.numel() - 1
+    out = _vp()
+    _check(_hec_from_csr(n, _ptr(rowptr), _ptr(col), _ptr(val), levels.h if levels is not None else None, int(ell_width),
+                         DTYPES[vdt], ctypes.byref(out), _stream(stream)), "hec_from_csr")
+    return Matrix(out.value, keep=(levels,))
+
+
+def hec_to_csr(matrix, levels=None, stream=None):
+    inf = matrix.info()
+    n = inf.n
+    nnz = int((matrix.arrays()["ell_col"] >= 0).sum().item()) + int(inf.tail_nnz)
+    rp = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    ci = torch.zeros(max(nnz, 1), dtype=torch.int32, device="cuda")
+    v = torch.zeros(max(nnz, 1), dtype=torch.float64, device="cuda")
+    _check(_hec_to_csr(matrix.h, levels.h if levels is not None else None, _ptr(rp), _ptr(ci), _ptr(v), _stream(stream)),
+           "hec_to_csr")
+    return rp, ci[:nnz], v[:nnz]
+
+
+def sptrsv_plan_create(matrix, levels, max_nrhs=1, block_threads=0, blocks_per_sm=0, wait_cycles=0,
+                       debug_unpublished_row=None):
+    t = HecTune(block_threads, blocks_per_sm, wait_cycles,
+                0 if debug_unpublished_row is None else int(debug_unpublished_row) + 1)
+    out = _vp()
+    _check(_sptrsv_plan_create(matrix.h, levels.h, int(max_nrhs), ctypes.byref(t), ctypes.byref(out)), "sptrsv_plan_create")
+    return Plan(out.value, keep=(matrix, levels))
+
+
+def _solve(fn, name, plan, b, x, stream):
+    nrhs = _nrhs(b)
+    if x is None:
+        x = torch.empty_like(b)
+    _check(fn(plan.h, nrhs, _ptr(b), _ld(b, nrhs), _ptr(x), _ld(x, nrhs), _stream(stream)), name)
+    return x
+
+
+def sptrsv_lower(plan, b, x=None, stream=None):
+    return _solve(_sptrsv_lower, "sptrsv_lower", plan, b, x, stream)
+
+
+def sptrsv_upper(plan, b, x=None, stream=None):
+    return _solve(_sptrsv_upper, "sptrsv_upper", plan, b, x, stream)
+
+
+def hec_sync_status(plan, stream=None):
+    return _hec_sync_status(plan.h, _stream(stream))
+
+
+def ilu_create(Lplan, Uplan, n_glob=None, ext2glob=None, owned=None):
+    n_ext = Lplan and Lplan._keep[0].info().n
+    if n_glob is None:
+        n_glob = n_ext
+    out = _vp()
+    _check(_ilu_create(Lplan.h, Uplan.h, int(n_glob), int(n_ext), _ptr(ext2glob), _ptr(owned), ctypes.byref(out)),
+           "ilu_create")
+    return Precond(out.value, keep=(Lplan, Uplan, ext2glob, owned))
+
+
+def ilu_apply(M, r, z=None, stream=None):
+    nrhs = _nrhs(r)
+    if z is None:
+        z = torch.empty_like(r)
+    _check(_ilu_apply(M.h, nrhs, _ptr(r), _ld(r, nrhs), _ptr(z), _ld(z, nrhs), _stream(stream)), "ilu_apply")
+    return z
+
+
+def spmv(A, x, y=None, alpha=1.0, beta=0.0, stream=None):
+    nrhs = _nrhs(x)
+    if y is None:
+        y = torch.zeros_like(x)
+    _check(_spmv(A.h, nrhs, float(alpha), _ptr(x), _ld(x, nrhs), float(beta), _ptr(y), _ld(y, nrhs), _stream(stream)),
+           "spmv")
+    return y
+
+
+def fgmres_solve(A, M, b, x=None, restart=30, rtol=1e-8, max_iters=1000, stream=None, raise_on_nonconvergence=True):
+    nrhs = _nrhs(b)
+    if x is None:
+        x = torch.zeros_like(b)
+    info = HecFgmresInfo()
+    st = _fgmres_solve(A.h, M.h if M is not None else None, nrhs, _ptr(b), _ld(b, nrhs), _ptr(x), _ld(x, nrhs),
+                       int(restart), float(rtol), int(max_iters), ctypes.byref(info), _stream(stream))
+    if st != OK and not (st == NOT_CONVERGED and not raise_on_nonconvergence):
+        raise HecError(st, "fgmres_solve")
+    return x, dict(iterations=info.iterations, restarts=info.restarts, converged=bool(info.converged),
+                   rel_residual=info.rel_residual, seconds=info.seconds)
+
+
+def ilu_factor(rowptr, col, val, k=0, stream=None):
+    n = rowptr.numel() - 1
+    L, U = _vp(), _vp()
+    _check(_ilu_factor(n, _ptr(rowptr), _ptr(col), _ptr(val), int(k), ctypes.byref(L), ctypes.byref(U), _stream(stream)),
+           "ilu_factor")
+    return Csr(L.value), Csr(U.value)
+
+
+# --- convenience: a full ILU solver assembled from the entry points ------------------------------
+
+class IluSolver:
+    """A ready-to-use preconditioned solver: levels, HEC factors, plans and the preconditioner for
+    given device CSR factors L, U (and optionally the matrix A for FGMRES)."""
+
+    def __init__(self, L, U, A=None, vdt="f64", max_nrhs=1, stream=None, **tune):
+        self.lvL = sptrsv_analyze(L[0], L[1], 0, stream)
+        self.lvU = sptrsv_analyze(U[0], U[1], 1, stream)
+        self.HL = hec_from_csr(*L, levels=self.lvL, vdt=vdt, stream=stream)
+        self.HU = hec_from_csr(*U, levels=self.lvU, vdt=vdt, stream=stream)
+        self.pL = sptrsv_plan_create(self.HL, self.lvL, max_nrhs, **tune)
+        self.pU = sptrsv_plan_create(self.HU, self.lvU, max_nrhs, **tune)
+        self.M = ilu_create(self.pL, self.pU)
+        self.A = hec_from_csr(*A, vdt="f64", stream=stream) if A is not None else None
+
+    def apply(self, r, z=None, stream=None):
+        return ilu_apply(self.M, r, z, stream)
+
+    def solve(self, b, x=None, restart=30, rtol=1e-8, max_iters=1000, stream=None, **kw):
+        return fgmres_solve(self.A, self.M, b, x, restart, rtol, max_iters, stream, **kw)
