@@ -156,6 +156,8 @@ typedef struct {
                                   solution is computed but never published to its dependents,
                                   so their waits run out and the call reports HEC_ERR_TIMEOUT;
                                   0 disables it, r + 1 selects row r */
+    int backoff_ns;         /* nanoseconds a warp sleeps between polls of an unpublished
+                               dependency (0 = poll continuously) */
 } hec_tune;
 
 /* A solve plan for one triangular factor: its HEC form and level analysis (both borrowed; they

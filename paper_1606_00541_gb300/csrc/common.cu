@@ -19,6 +19,7 @@ hec_status set_error(hec_status s, const std::string& msg) {
 }
 
 hec_status cuda_error(cudaError_t e, const char* what) {
+    cudaGetLastError();  // a non-sticky error must not be reported again by the next call
     std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
     if (e == cudaErrorMemoryAllocation) return set_error(HEC_ERR_OOM, m);
     return set_error(HEC_ERR_CUDA, m);

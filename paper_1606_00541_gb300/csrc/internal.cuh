@@ -89,8 +89,11 @@ struct sptrsv_plan {
     int threads = 256, blocks = 0;
     long long wait_cycles = 2000000000LL;
     int skip_row = -1;         // fault injection: row never published (tests only)
+    int backoff_ns = 0;        // sleep between dependency polls
     void* xp = nullptr;        // internal solution in level order, n * max_nrhs of the work type
     int* status = nullptr;     // device status word
+    int2* chunks[5] = {};      // level-aligned chunk tables for 32, 16, 8, 4, 2 rows per warp step
+    int nchunks[5] = {};
 };
 
 struct ilu_precond {

@@ -41,6 +41,9 @@ struct SweepParams {
     int* status;
     long long budget;
     int skip_row;
+    int backoff_ns;
+    const int2* __restrict__ chunks;  // (first row, rows) of each level-aligned chunk
+    int nchunks;
 };
 
 template <typename XT> struct Acc { typedef float T; };
@@ -56,45 +59,191 @@ __device__ __forceinline__ float wait_x(const float* p, int* st, long long b) { 
 __device__ __forceinline__ void publish_x(double* p, double v) { publish_f64(p, v); }
 __device__ __forceinline__ void publish_x(float* p, float v) { publish_f32(p, v); }
 
-template <typename VT, typename XT, int KP>
+// Raw word access to the internal solution (the sentinel test needs the bits).
+template <typename XT> struct Word;
+template <> struct Word<double> {
+    typedef unsigned long long T;
+    static constexpr T kSent = kSent64;
+    __device__ static T load(const double* p) { return ld_relaxed_u64(p); }
+    __device__ static double val(T w) { return __longlong_as_double((long long)w); }
+};
+template <> struct Word<float> {
+    typedef unsigned int T;
+    static constexpr T kSent = kSent32;
+    __device__ static T load(const float* p) { return ld_relaxed_u32(p); }
+    __device__ static float val(T w) { return __uint_as_float(w); }
+};
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// The warp waits, converged, until every lane's pending dependency words have been published.
+// pending: bit k set = slot k of this lane still outstanding.  Polls are issued for all
+// outstanding slots at once.  Returns false (and records DEV_TIMEOUT) when the budget runs out.
+template <typename XT, int NS>
+__device__ __forceinline__ void warp_wait(const XT* const (&addr)[NS], typename Word<XT>::T (&raw)[NS],
+                                          unsigned pending, int* status, long long budget, int backoff_ns) {
+    typedef Word<XT> W;
+    if (!__any_sync(kFull, pending)) return;
+    const long long t0 = clock64();
+    for (unsigned it = 1;; ++it) {
+        if (backoff_ns) __nanosleep(backoff_ns);
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            if (pending & (1u << k)) {
+                raw[k] = W::load(addr[k]);
+                if (raw[k] != W::kSent) pending &= ~(1u << k);
+            }
+        }
+        if (!__any_sync(kFull, pending)) return;
+        if ((it & 31u) == 0u) {
+            bool give_up = (clock64() - t0 > budget) || (ld_relaxed_u32(status) != 0u);
+            if (__any_sync(kFull, give_up)) {
+                record(status, HEC_ERR_TIMEOUT);
+#pragma unroll
+                for (int k = 0; k < NS; ++k)
+                    if (pending & (1u << k)) raw[k] = 0;
+                return;
+            }
+        }
+    }
+}
+
+constexpr int kTailBatch = 4;
+
+// Up to NS dependencies of one lane: their solution addresses, the coefficients, and the words
+// read so far.  Entries are accumulated in slot order, which is the row's column order.
+template <typename XT, typename AT, int NS>
+struct DepBatch {
+    typedef Word<XT> W;
+    const XT* addr[NS];
+    typename W::T raw[NS];
+    AT v[NS];
+    unsigned valid, pend;
+    __device__ __forceinline__ void clear(const XT* base) {
+        valid = pend = 0;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            addr[k] = base;
+            raw[k] = 0;
+            v[k] = AT(0);
+        }
+    }
+    __device__ __forceinline__ void set(int k, const XT* a, AT coef) {
+        addr[k] = a;
+        v[k] = coef;
+        valid |= 1u << k;
+        pend |= 1u << k;
+    }
+    template <typename VT>
+    __device__ __forceinline__ void load_tail(const int* __restrict__ tcol, const VT* __restrict__ tv, int t0, int tb,
+                                              int tl, const XT* xp, int K, int q) {
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            if (tb + k < tl) {
+                const int cc = __ldg(tcol + t0 + tb + k);
+                set(k, xp + (long)cc * K + q, ldv<VT, AT>(tv + t0 + tb + k));
+            }
+        }
+    }
+    __device__ __forceinline__ void poll() {
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            if (pend & (1u << k)) {
+                raw[k] = W::load(addr[k]);
+                if (raw[k] != W::kSent) pend &= ~(1u << k);
+            }
+        }
+    }
+    __device__ __forceinline__ void wait(int* status, long long budget, int backoff_ns) {
+        warp_wait<XT, NS>(addr, raw, pend, status, budget, backoff_ns);
+    }
+    __device__ __forceinline__ AT accumulate(AT acc) const {
+#pragma unroll
+        for (int k = 0; k < NS; ++k)
+            if (valid & (1u << k)) acc = fma(-v[k], (AT)W::val(raw[k]), acc);
+        return acc;
+    }
+};
+
+template <typename VT, typename XT, int KP, int WMAX>
 __global__ void __launch_bounds__(256) k_sweep(SweepParams p) {
     typedef typename Acc<XT>::T AT;
+    typedef Word<XT> W;
     constexpr int RPW = 32 / KP;  // rows per warp step
     const int lane = threadIdx.x & 31;
     const int rsub = lane / KP, q = lane % KP;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    const int nchunks = (p.n + RPW - 1) / RPW;
+    const int nchunks = p.nchunks;
     const VT* __restrict__ ev = (const VT*)p.ell_val;
     const VT* __restrict__ tv = (const VT*)p.tval;
     XT* xp = (XT*)p.xp;
     const int K = p.K;
+    // A chunk is up to RPW consecutive rows of ONE level, so no row of a chunk depends on another
+    // row of the same chunk and the lockstep waits below cannot wait on the warp itself.  The loop
+    // trip counts are warp-uniform, so the warp stays converged throughout.
     for (int c = gw; c < nchunks; c += nw) {
-        const int r = c * RPW + rsub;
-        if (r >= p.n || q >= K) continue;
-        const int gr = p.gather ? __ldg(p.gather + r) : r;
-        AT acc = (AT)__ldg(p.b + (long)gr * p.ldb + q);
-        // slab entries of row r (padding, column -1, only after the row's entries)
-        for (int k = 0; k < p.w; ++k) {
-            const long s = (long)k * p.ld + r;
-            const int cc = __ldg(p.ell_col + s);
-            if (cc < 0) break;
-            const AT v = ldv<VT, AT>(ev + s);
-            const AT xc = (AT)wait_x(xp + (long)cc * K + q, p.status, p.budget);
-            acc = fma(-v, xc, acc);
+        const int2 ch = __ldg(p.chunks + c);
+        const int r = ch.x + rsub;
+        const bool act = rsub < ch.y && q < K;
+        // Everything that does not depend on other rows is loaded before the first wait, so that
+        // after the last dependency arrives only arithmetic and the two stores remain.
+        AT acc = AT(0), diag = AT(1);
+        int t0 = 0, tl = 0, sr = -1;
+        if (act) {
+            const int gr = p.gather ? __ldg(p.gather + r) : r;
+            acc = (AT)__ldg(p.b + (long)gr * p.ldb + q);
+            t0 = __ldg(p.tptr + r);
+            const int t1 = __ldg(p.tptr + r + 1) - 1;
+            tl = t1 - t0;
+            diag = ldv<VT, AT>(tv + t1);  // the diagonal is the last tail entry
+            sr = p.scatter ? __ldg(p.scatter + r) : r;
         }
-        // tail: overflow off-diagonals, then the diagonal
-        const int t0 = __ldg(p.tptr + r), t1 = __ldg(p.tptr + r + 1) - 1;
-        for (int t = t0; t < t1; ++t) {
-            const int cc = __ldg(p.tcol + t);
-            const AT v = ldv<VT, AT>(tv + t);
-            const AT xc = (AT)wait_x(xp + (long)cc * K + q, p.status, p.budget);
-            acc = fma(-v, xc, acc);
+        DepBatch<XT, AT, WMAX> slab;
+        slab.clear(xp);
+#pragma unroll
+        for (int k = 0; k < WMAX; ++k) {
+            if (act && k < p.w) {
+                const long s = (long)k * p.ld + r;
+                const int cc = __ldg(p.ell_col + s);
+                if (cc >= 0) slab.set(k, xp + (long)cc * K + q, ldv<VT, AT>(ev + s));
+            }
         }
-        const AT xr = acc / ldv<VT, AT>(tv + t1);
-        if (r != p.skip_row) publish_x(xp + (long)r * K + q, (XT)xr);
-        const int sr = p.scatter ? __ldg(p.scatter + r) : r;
-        if (sr >= 0) p.x[(long)sr * p.ldx + q] = (double)xr;
+        const int tmax = __reduce_max_sync(kFull, tl);
+        DepBatch<XT, AT, kTailBatch> tail;
+        tail.clear(xp);
+        if (tmax > 0) tail.load_tail(p.tcol, tv, t0, 0, tl, xp, K, q);
+        slab.poll();
+        slab.wait(p.status, p.budget, p.backoff_ns);
+        acc = slab.accumulate(acc);
+        // wider slabs: the remaining slots one at a time (same order)
+        for (int k = WMAX; k < p.w; ++k) {
+            DepBatch<XT, AT, 1> one;
+            one.clear(xp);
+            if (act) {
+                const long s = (long)k * p.ld + r;
+                const int cc = __ldg(p.ell_col + s);
+                if (cc >= 0) one.set(0, xp + (long)cc * K + q, ldv<VT, AT>(ev + s));
+            }
+            one.poll();
+            one.wait(p.status, p.budget, p.backoff_ns);
+            acc = one.accumulate(acc);
+        }
+        // tail overflow entries in ascending new column, kTailBatch at a time (warp-uniform count)
+        for (int tb = 0; tb < tmax; tb += kTailBatch) {
+            if (tb > 0) {
+                tail.clear(xp);
+                tail.load_tail(p.tcol, tv, t0, tb, tl, xp, K, q);
+            }
+            tail.poll();
+            tail.wait(p.status, p.budget, p.backoff_ns);
+            acc = tail.accumulate(acc);
+        }
+        if (act) {
+            const AT xr = acc / diag;
+            if (r != p.skip_row) publish_x(xp + (long)r * K + q, (XT)xr);
+            if (sr >= 0) p.x[(long)sr * p.ldx + q] = (double)xr;
+        }
     }
 }
 
@@ -109,26 +258,30 @@ __global__ void k_fill_sentinel(XT* xp, long count) {
 }
 
 std::mutex g_occ_mu;
-std::unordered_map<const void*, int> g_occ;
+std::unordered_map<const void*, int> g_occ[9];  // per block size (threads / 32)
 
 int occupancy(const void* k, int threads) {
     std::lock_guard<std::mutex> g(g_occ_mu);
-    auto it = g_occ.find(k);
-    if (it != g_occ.end()) return it->second;
+    auto& tbl = g_occ[(threads / 32) % 9];
+    auto it = tbl.find(k);
+    if (it != tbl.end()) return it->second;
     int nb = max_coop_blocks(k, threads, 0);
-    g_occ[k] = nb;
+    tbl[k] = nb;
     return nb;
 }
 
-template <typename VT, typename XT, int KP>
+template <typename VT, typename XT, int KP, int WMAX>
 hec_status launch_sweep(const sptrsv_plan* pl, SweepParams& sp, cudaStream_t s) {
-    const void* k = (const void*)k_sweep<VT, XT, KP>;
+    const void* k = (const void*)k_sweep<VT, XT, KP, WMAX>;
     const int threads = pl->threads;
     int per_sm = occupancy(k, threads);
     if (per_sm <= 0) return set_error(HEC_ERR_CUDA, "sweep kernel cannot be resident");
     if (pl->blocks > 0) per_sm = std::min(per_sm, pl->blocks);
-    constexpr int RPW = 32 / KP;
-    long nchunks = (sp.n + RPW - 1) / RPW;
+    constexpr int kp_idx = KP == 1 ? 0 : KP == 2 ? 1 : KP == 4 ? 2 : KP == 8 ? 3 : 4;
+    if (!pl->chunks[kp_idx]) return set_error(HEC_ERR_INVALID_ARG, "sweep: nrhs above the plan's max_nrhs");
+    sp.chunks = pl->chunks[kp_idx];
+    sp.nchunks = pl->nchunks[kp_idx];
+    long nchunks = sp.nchunks;
     long want = (nchunks + threads / 32 - 1) / (threads / 32);
     int blocks = (int)std::max(1L, std::min((long)per_sm * num_sms(), want));
     long count = (long)sp.n * sp.K;
@@ -144,16 +297,76 @@ hec_status launch_sweep(const sptrsv_plan* pl, SweepParams& sp, cudaStream_t s) 
     return HEC_OK;
 }
 
-template <typename VT, typename XT>
+template <typename VT, typename XT, int WMAX>
 hec_status dispatch_k(const sptrsv_plan* pl, SweepParams& sp, cudaStream_t s) {
-    if (sp.K <= 1) return launch_sweep<VT, XT, 1>(pl, sp, s);
-    if (sp.K <= 2) return launch_sweep<VT, XT, 2>(pl, sp, s);
-    if (sp.K <= 4) return launch_sweep<VT, XT, 4>(pl, sp, s);
-    if (sp.K <= 8) return launch_sweep<VT, XT, 8>(pl, sp, s);
-    return launch_sweep<VT, XT, 16>(pl, sp, s);
+    if (sp.K <= 1) return launch_sweep<VT, XT, 1, WMAX>(pl, sp, s);
+    if (sp.K <= 2) return launch_sweep<VT, XT, 2, WMAX>(pl, sp, s);
+    if (sp.K <= 4) return launch_sweep<VT, XT, 4, WMAX>(pl, sp, s);
+    if (sp.K <= 8) return launch_sweep<VT, XT, 8, WMAX>(pl, sp, s);
+    return launch_sweep<VT, XT, 16, WMAX>(pl, sp, s);
+}
+
+// slab slots held in registers: 4 covers the 5- and 7-point ILU(0) factors, 8 the wider ones
+template <typename VT, typename XT>
+hec_status dispatch_w(const sptrsv_plan* pl, SweepParams& sp, cudaStream_t s) {
+    if (sp.w <= 4) return dispatch_k<VT, XT, 4>(pl, sp, s);
+    return dispatch_k<VT, XT, 8>(pl, sp, s);
 }
 
 size_t work_size(hec_dtype d) { return d == HEC_F64 ? 8 : 4; }
+
+// Level-aligned chunks of at most rpw rows: level l contributes ceil(N_l / rpw) chunks.
+__global__ void k_chunk_counts(int nlev, const int* __restrict__ level_ptr, int rpw, int* cnt) {
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < nlev) cnt[l] = (level_ptr[l + 1] - level_ptr[l] + rpw - 1) / rpw;
+}
+
+__global__ void k_chunk_table(int nlev, const int* __restrict__ level_ptr, const int* __restrict__ cptr, int rpw,
+                              int nchunks, int2* tbl) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nchunks) return;
+    int lo = 0, hi = nlev - 1;  // last level l with cptr[l] <= c
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (cptr[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    int row0 = level_ptr[lo] + (c - cptr[lo]) * rpw;
+    tbl[c] = make_int2(row0, min(rpw, level_ptr[lo + 1] - row0));
+}
+
+hec_status build_chunks(sptrsv_plan* p) {
+    const hec_levels* lv = p->lv;
+    const int nlev = lv->nlev;
+    int* cptr = nullptr;
+    HEC_CHECK(dalloc(&cptr, (size_t)nlev + 1));
+    hec_status st = HEC_OK;
+    cudaStream_t s = 0;
+    for (int i = 0; i < 5 && st == HEC_OK; ++i) {
+        const int kp = 1 << i, rpw = 32 / kp;
+        if (i > 0 && (kp >> 1) >= p->max_nrhs) break;  // only the widths this plan can be called with
+        if (nlev > 0) {
+            k_chunk_counts<<<(nlev + 255) / 256, 256, 0, s>>>(nlev, lv->level_ptr, rpw, cptr);
+            count_launch();
+        }
+        if ((st = exclusive_scan_i32(cptr, cptr, nlev, true, s))) break;
+        int nc = 0;
+        if (cudaMemcpy(&nc, cptr + nlev, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            st = cuda_error(cudaGetLastError(), "chunk table");
+            break;
+        }
+        if ((st = dalloc(&p->chunks[i], (size_t)nc))) break;
+        p->nchunks[i] = nc;
+        if (nc > 0) {
+            k_chunk_table<<<(nc + 255) / 256, 256, 0, s>>>(nlev, lv->level_ptr, cptr, rpw, nc, p->chunks[i]);
+            count_launch();
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_error(e, "chunk table");
+    }
+    cudaFree(cptr);
+    return st;
+}
 
 }  // namespace
 
@@ -181,10 +394,11 @@ hec_status sweep(const sptrsv_plan* pl, int nrhs, const double* b, int ldb, cons
     sp.status = pl->status;
     sp.budget = pl->wait_cycles;
     sp.skip_row = pl->skip_row;
+    sp.backoff_ns = pl->backoff_ns;
     switch (T->vdt) {
-        case HEC_F64: return dispatch_k<double, double>(pl, sp, s);
-        case HEC_F32: return dispatch_k<float, float>(pl, sp, s);
-        default: return dispatch_k<__nv_bfloat16, float>(pl, sp, s);
+        case HEC_F64: return dispatch_w<double, double>(pl, sp, s);
+        case HEC_F32: return dispatch_w<float, float>(pl, sp, s);
+        default: return dispatch_w<__nv_bfloat16, float>(pl, sp, s);
     }
 }
 
@@ -206,6 +420,7 @@ void free_plan(sptrsv_plan* p) {
     if (!p) return;
     cudaFree(p->xp);
     cudaFree(p->status);
+    for (int i = 0; i < 5; ++i) cudaFree(p->chunks[i]);
     delete p;
 }
 
@@ -229,6 +444,7 @@ HEC_API hec_status sptrsv_plan_create(const hec_matrix* tri, const hec_levels* l
         if (tune->blocks_per_sm) p->blocks = tune->blocks_per_sm;
         if (tune->wait_cycles) p->wait_cycles = tune->wait_cycles;
         if (tune->debug_unpublished_row > 0) p->skip_row = tune->debug_unpublished_row - 1;
+        if (tune->backoff_ns > 0) p->backoff_ns = tune->backoff_ns;
     }
     if (p->threads % 32 || p->threads < 32 || p->threads > 256) {
         delete p;
@@ -237,6 +453,7 @@ HEC_API hec_status sptrsv_plan_create(const hec_matrix* tri, const hec_levels* l
     hec_status st = dmalloc(&p->xp, work_size(tri->vdt) * (size_t)tri->n * max_nrhs + 16);
     if (st == HEC_OK) st = dalloc(&p->status, 1);
     if (st == HEC_OK && cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) st = cuda_error(cudaGetLastError(), "memset");
+    if (st == HEC_OK) st = build_chunks(p);
     if (st != HEC_OK) { free_plan(p); return st; }
     *out = p;
     return HEC_OK;

@@ -43,7 +43,8 @@ class HecMatrixInfo(ctypes.Structure):
 
 
 class HecTune(ctypes.Structure):
-    _fields_ = [("block_threads", _i), ("blocks_per_sm", _i), ("wait_cycles", _ll), ("debug_unpublished_row", _i)]
+    _fields_ = [("block_threads", _i), ("blocks_per_sm", _i), ("wait_cycles", _ll), ("debug_unpublished_row", _i),
+                ("backoff_ns", _i)]
 
 
 class HecFgmresInfo(ctypes.Structure):
@@ -284,9 +285,9 @@ def hec_to_csr(matrix, levels=None, stream=None):
 
 
 def sptrsv_plan_create(matrix, levels, max_nrhs=1, block_threads=0, blocks_per_sm=0, wait_cycles=0,
-                       debug_unpublished_row=None):
+                       debug_unpublished_row=None, backoff_ns=0):
     t = HecTune(block_threads, blocks_per_sm, wait_cycles,
-                0 if debug_unpublished_row is None else int(debug_unpublished_row) + 1)
+                0 if debug_unpublished_row is None else int(debug_unpublished_row) + 1, backoff_ns)
     out = _vp()
     _check(_sptrsv_plan_create(matrix.h, levels.h, int(max_nrhs), ctypes.byref(t), ctypes.byref(out)), "sptrsv_plan_create")
     return Plan(out.value, keep=(matrix, levels))
