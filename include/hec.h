@@ -26,6 +26,8 @@
 #ifndef HEC_H
 #define HEC_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -252,6 +254,36 @@ hec_status hec_csr_destroy(hec_csr* M);
  * a nonzero diagonal in every row; ZERO_PIVOT if an eliminated pivot is zero.  Synchronizes. */
 hec_status ilu_factor(int n, const int* rowptr, const int* col, const double* val, int k,
                       hec_csr** L, hec_csr** U, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Allocation-free sweep (the paper has no counterpart: this is a deployment convenience)      */
+/* ---------------------------------------------------------------------------------------- */
+
+/* The same triangular sweep as sptrsv_lower (tri->uplo == 0) or sptrsv_upper (tri->uplo == 1),
+ * for callers that must not allocate device memory when they solve: their device memory is
+ * owned and accounted for by another allocator, or every byte is reserved up front and later
+ * allocation is forbidden, or they cannot afford a cudaMalloc (which may synchronize the
+ * device) inside a latency-critical loop.  This call allocates nothing: the scratch it needs
+ * (chunk table, level-ordered solution, status word) lives in one static device buffer of
+ * sptrsv_noalloc_capacity() bytes (32 MiB), which every GPU that loads the library holds until
+ * the process exits.  The caller still passes tri and lv (built once with sptrsv_analyze and
+ * hec_from_csr) and the device arrays b and x, with the layout of sptrsv_lower.
+ *   - Size limit: a problem whose scratch (n * nrhs * 8 bytes for FP64 factors, 4 for FP32 /
+ *     BF16, plus the chunk table) exceeds the buffer is rejected with HEC_ERR_INVALID_ARG and a
+ *     message giving the bytes needed; use sptrsv_lower / sptrsv_upper for those.
+ *   - The first call on a device looks up the buffer's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture.
+ *   - All calls share the one buffer and it keeps the last call's contents; every call resets
+ *     the parts that must start fresh.  Calls whose work overlaps on the GPU (different
+ *     streams, or different host threads on one device) race on the buffer: serialize them.
+ *   - status_out (host, may be NULL): when given, the call synchronizes `stream` and stores the
+ *     device-side status (0, or HEC_ERR_TIMEOUT when a dependency wait ran out), also returned.
+ *     When NULL the call is asynchronous and device-side failures are not reported. */
+hec_status sptrsv_solve_noalloc(const hec_matrix* tri, const hec_levels* lv, int nrhs,
+                                const double* b, int ldb, double* x, int ldx, int* status_out,
+                                void* stream);
+/* Bytes of the static buffer used by sptrsv_solve_noalloc. */
+size_t sptrsv_noalloc_capacity(void);
 
 #ifdef __cplusplus
 }
