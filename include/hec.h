@@ -68,6 +68,9 @@ long long hec_launch_count(void);
  * since the last reset (reset != 0 clears the record).  Off by default. */
 hec_status hec_profile_enable(int on);
 hec_status hec_profile_read(double* sweep_ms, long long* sweep_launches, int reset);
+/* The same record for other kernel classes (not reset): 0 sweeps, 1 SpMV, 2 Gram-Schmidt dots
+ * and updates, 3 the small Arnoldi kernels, 4 vector scale/copy/update, 5 sentinel fills. */
+hec_status hec_profile_read_category(int category, double* ms, long long* launches);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Level analysis: Eq. 2 (levels), Eq. 3 (map m), Alg. 1 steps 1-2; upper factor by the       */

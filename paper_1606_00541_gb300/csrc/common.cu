@@ -160,17 +160,22 @@ hec_status exclusive_scan_i32(const int* in, int* out, int n, bool write_total, 
 
 }  // namespace hec
 
-// ---- sweep timing (measurement only) ------------------------------------------------------
+// ---- kernel timing by category (measurement only) ------------------------------------------
 namespace hec {
 namespace {
+struct ProfEntry {
+    cudaEvent_t a, b;
+    int cat;
+};
 std::mutex g_prof_mu;
 bool g_prof_on = false;
-std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_used, g_prof_free;
+std::vector<ProfEntry> g_prof_used;
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_free;
 }  // namespace
 
 bool profiling() { return g_prof_on; }
 
-void profile_begin(cudaStream_t s, void** token) {
+void profile_begin(cudaStream_t s, void** token, int cat) {
     *token = nullptr;
     if (!g_prof_on) return;
     std::lock_guard<std::mutex> g(g_prof_mu);
@@ -185,7 +190,7 @@ void profile_begin(cudaStream_t s, void** token) {
         }
     }
     cudaEventRecord(ev.first, s);
-    g_prof_used.push_back(ev);
+    g_prof_used.push_back({ev.first, ev.second, cat});
     *token = (void*)(g_prof_used.size());
 }
 
@@ -193,7 +198,22 @@ void profile_end(cudaStream_t s, void* token) {
     if (!token) return;
     std::lock_guard<std::mutex> g(g_prof_mu);
     size_t idx = (size_t)token - 1;
-    if (idx < g_prof_used.size()) cudaEventRecord(g_prof_used[idx].second, s);
+    if (idx < g_prof_used.size()) cudaEventRecord(g_prof_used[idx].b, s);
+}
+
+static void prof_sum(int cat, double* ms_out, long long* n_out) {
+    double tot = 0.0;
+    long long cnt = 0;
+    for (auto& ev : g_prof_used) {
+        if (ev.cat != cat) continue;
+        cudaEventSynchronize(ev.b);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev.a, ev.b) == cudaSuccess) tot += ms;
+        else cudaGetLastError();
+        cnt++;
+    }
+    if (ms_out) *ms_out = tot;
+    if (n_out) *n_out = cnt;
 }
 }  // namespace hec
 
@@ -202,19 +222,17 @@ HEC_API hec_status hec_profile_enable(int on) {
     return HEC_OK;
 }
 
+HEC_API hec_status hec_profile_read_category(int category, double* ms, long long* launches) {
+    std::lock_guard<std::mutex> g(hec::g_prof_mu);
+    hec::prof_sum(category, ms, launches);
+    return HEC_OK;
+}
+
 HEC_API hec_status hec_profile_read(double* sweep_ms, long long* launches, int reset) {
     std::lock_guard<std::mutex> g(hec::g_prof_mu);
-    double tot = 0.0;
-    for (auto& ev : hec::g_prof_used) {
-        cudaEventSynchronize(ev.second);
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) tot += ms;
-        else cudaGetLastError();
-    }
-    if (sweep_ms) *sweep_ms = tot;
-    if (launches) *launches = (long long)hec::g_prof_used.size();
+    hec::prof_sum(0, sweep_ms, launches);
     if (reset) {
-        for (auto& ev : hec::g_prof_used) hec::g_prof_free.push_back(ev);
+        for (auto& ev : hec::g_prof_used) hec::g_prof_free.push_back({ev.a, ev.b});
         hec::g_prof_used.clear();
     }
     return HEC_OK;

@@ -44,9 +44,17 @@ template <typename T>
 hec_status dalloc(T** p, size_t count) { return dmalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16); }
 
 int num_sms();
-// measurement hooks around sweep launches (no-ops unless hec_profile_enable(1))
-void profile_begin(cudaStream_t s, void** token);
+// measurement hooks around kernel launches (no-ops unless hec_profile_enable(1)); categories:
+enum ProfCat { PROF_SWEEP = 0, PROF_SPMV = 1, PROF_GS = 2, PROF_ARNOLDI = 3, PROF_VEC = 4, PROF_FILL = 5 };
+void profile_begin(cudaStream_t s, void** token, int cat = PROF_SWEEP);
 void profile_end(cudaStream_t s, void* token);
+// RAII bracket for one launch
+struct ProfScope {
+    cudaStream_t s;
+    void* tok = nullptr;
+    ProfScope(cudaStream_t st, int cat) : s(st) { profile_begin(s, &tok, cat); }
+    ~ProfScope() { profile_end(s, tok); }
+};
 int max_coop_blocks(const void* kernel, int threads, size_t smem);  // resident blocks per SM
 
 // ---- device status word codes -------------------------------------------------------------

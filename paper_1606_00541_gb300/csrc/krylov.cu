@@ -2,15 +2,30 @@
 // FP64, Sec. 4; this library uses the flexible variant so that any preconditioner stage may
 // change between iterations).
 //
-// Vectors of nrhs right-hand sides are row-major n x K (K = nrhs).  Reductions are
-// deterministic: every block writes its partial sums and a second kernel adds them in a fixed
-// order.  Each inner iteration runs: z_j = M^-1 v_j (ilu_apply), w = A z_j (SpMV), classical
-// Gram-Schmidt twice (h = V^T w; w -= V h), ||w||, and the small Hessenberg update on the host.
+// Vectors of nrhs right-hand sides are row-major n x K (K = nrhs); each right-hand side has its
+// own Krylov space and the kernels run them batched.  Reductions are deterministic: every block
+// writes its partial sums and a second kernel adds them in a fixed order.
+//
+// Each inner iteration is a fixed sequence of launches with no host round trip:
+//   z_j = M^-1 v_j (ilu_apply), w = A z_j (SpMV),
+//   classical Gram-Schmidt h = V^T w, w -= V h, with ||w||^2 before and after,
+//   a second (re-orthogonalization) pass only when ||w|| dropped below ||w_0|| / sqrt(2)
+//     (the "twice is enough" criterion; the pass is skipped on the device otherwise),
+//   the Hessenberg column, Givens rotations and the convergence test in a one-block kernel,
+//   and w /= h_{j+1,j}.
+// The host stays one iteration ahead of the device and reads a per-iteration "still active"
+// flag through pinned memory, so the GPU never waits for the host inside a restart cycle.  The
+// host synchronizes once per restart to check the true residual.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace hec {
 namespace {
@@ -52,16 +67,19 @@ __global__ void k_copy(long total, int K, const double* __restrict__ src, int ld
     }
 }
 
-// partial[g][blk][q] for the dot products <V_a, w>, a = a0 + g, over this block's rows
+// partial[a][blk][q] = this block's share of <V_a, w> for a < count, and of <w, w> at index
+// count when `self` is set.  A gate flag of 0 skips the work (re-orthogonalization pass).
 template <int KP>
 __global__ void __launch_bounds__(kThreads) k_multidot(int n, int K, const double* __restrict__ V, long vstride,
-                                                       int count, const double* __restrict__ w,
-                                                       double* __restrict__ partial) {
+                                                       int count, int self, const double* __restrict__ w,
+                                                       double* __restrict__ partial, const int* gate) {
+    if (gate && *gate == 0) return;
     constexpr int RPB = kThreads / KP;
     __shared__ double red[kThreads / 32][kDotGroup][KP];
     const int q = threadIdx.x % KP;
     const int a0 = blockIdx.y * kDotGroup;
-    const int na = min(kDotGroup, count - a0);
+    const int total = count + self;
+    const int na = min(kDotGroup, total - a0);
     double acc[kDotGroup];
 #pragma unroll
     for (int g = 0; g < kDotGroup; ++g) acc[g] = 0.0;
@@ -69,8 +87,13 @@ __global__ void __launch_bounds__(kThreads) k_multidot(int n, int K, const doubl
         for (long r = (long)blockIdx.x * RPB + threadIdx.x / KP; r < n; r += (long)gridDim.x * RPB) {
             const double wv = w[r * K + q];
 #pragma unroll
-            for (int g = 0; g < kDotGroup; ++g)
-                if (g < na) acc[g] = fma(V[(long)(a0 + g) * vstride + r * K + q], wv, acc[g]);
+            for (int g = 0; g < kDotGroup; ++g) {
+                if (g < na) {
+                    const int a = a0 + g;
+                    const double va = a < count ? V[(long)a * vstride + r * K + q] : wv;
+                    acc[g] = fma(va, wv, acc[g]);
+                }
+            }
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -90,28 +113,21 @@ __global__ void __launch_bounds__(kThreads) k_multidot(int n, int K, const doubl
     }
 }
 
-// out[a][q] = sum over blocks of partial[a][blk][q] (+ out when accumulate)
-__global__ void k_reduce(int count, int nblk, int K, const double* __restrict__ partial, double* out, int accumulate) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+// out[a][q] = sum over blocks of partial[a][blk][q]: one warp per output, fixed order
+__global__ void k_reduce(int count, int nblk, int K, const double* __restrict__ partial, double* __restrict__ out,
+                         const int* gate) {
+    if (gate && *gate == 0) return;
+    const int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (idx >= count * K) return;
-    int a = idx / K, q = idx % K;
+    const int a = idx / K, q = idx % K;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += partial[((long)a * nblk + b) * K + q];
-    out[idx] = accumulate ? out[idx] + s : s;
+    for (int b = lane; b < nblk; b += 32) s += partial[((long)a * nblk + b) * K + q];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[idx] = s;
 }
 
-// w -= sum_a V_a h[a]   (classical Gram-Schmidt update)
-__global__ void k_cgs_update(long total, int K, const double* __restrict__ V, long vstride, int count,
-                             const double* __restrict__ h, double* __restrict__ w) {
-    long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long st = (long)gridDim.x * blockDim.x;
-    for (; e < total; e += st) {
-        int q = (int)(e % K);
-        double s = w[e];
-        for (int a = 0; a < count; ++a) s = fma(-V[(long)a * vstride + e], h[a * K + q], s);
-        w[e] = s;
-    }
-}
 
 __global__ void k_scale(long total, int K, double* __restrict__ v, const double* __restrict__ f) {
     long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -133,36 +149,221 @@ __global__ void k_update_x(long total, int K, const double* __restrict__ Z, long
     }
 }
 
+// Arnoldi state of one restart cycle, all on the device.
+struct ArnoldiState {
+    double* H;     // [(m+1) * m * K]  column j, row a at (a*m + j)*K + q
+    double* cs;    // [m*K]
+    double* sn;    // [m*K]
+    double* g;     // [(m+1)*K]
+    double* y;     // [m*K]
+    double* h1;    // [(m+2)*K]  first pass dots, then <w,w> before the pass at index j+1
+    double* h2;    // [(m+1)*K]  second pass dots
+    double* n1;    // [K]  ||w||^2 after the first pass
+    double* n2;    // [K]  ||w||^2 after the second pass
+    double* f;     // [K]  scale for w
+    double* bnorm; // [K]
+    int* active;   // [K]
+    int* jq;       // [K]  columns used by each right-hand side in this cycle
+    int* reorth;   // [1]  second pass needed
+    int* any;      // [1]  some right-hand side still active after this iteration
+};
+
+// Hessenberg column j of right-hand side q from the projections st.h1[0..j] and the norm hn
+// of the orthogonalized vector: previous Givens rotations, the new rotation, the residual
+// estimate g and the convergence test; f = 1 / hn while the right-hand side stays active.
+// Returns whether it is still active.
+__device__ bool arnoldi_column(const ArnoldiState& st, int K, int j, int m, double rtol, int q, double hn) {
+    if (!st.active[q]) {
+        st.f[q] = 0.0;
+        return false;
+    }
+    {
+        {
+            double* H = st.H;
+            for (int a = 0; a <= j; ++a) H[((size_t)a * m + j) * K + q] = st.h1[a * K + q];
+            H[((size_t)(j + 1) * m + j) * K + q] = hn;
+            for (int a = 0; a < j; ++a) {
+                const double c = st.cs[a * K + q], s = st.sn[a * K + q];
+                const double h0 = H[((size_t)a * m + j) * K + q], h1 = H[((size_t)(a + 1) * m + j) * K + q];
+                H[((size_t)a * m + j) * K + q] = c * h0 + s * h1;
+                H[((size_t)(a + 1) * m + j) * K + q] = -s * h0 + c * h1;
+            }
+            const double h0 = H[((size_t)j * m + j) * K + q], h1 = hn;
+            const double den = sqrt(h0 * h0 + h1 * h1);
+            const double c = den == 0.0 ? 1.0 : h0 / den, s = den == 0.0 ? 0.0 : h1 / den;
+            st.cs[j * K + q] = c;
+            st.sn[j * K + q] = s;
+            H[((size_t)j * m + j) * K + q] = c * h0 + s * h1;
+            const double gj = st.g[j * K + q];
+            st.g[(j + 1) * K + q] = -s * gj;
+            st.g[j * K + q] = c * gj;
+            st.jq[q] = j + 1;
+            const bool done = fabs(st.g[(j + 1) * K + q]) <= rtol * st.bnorm[q] || hn == 0.0 || j + 1 >= m;
+            if (done) st.active[q] = 0;
+            st.f[q] = (!done && hn > 0.0) ? 1.0 / hn : 0.0;
+            return !done;
+        }
+    }
+}
+
+// One Arnoldi step after w = A z_j, as one cooperative persistent launch: modified
+// Gram-Schmidt against v_0..v_j (h_a = <v_a, w>; w -= h_a v_a, one grid-wide reduction per a),
+// ||w||, the Hessenberg column with its rotations and the convergence test (block 0), and
+// w /= h_{j+1,j}.  FP64 throughout.  Reductions are deterministic: each block writes its partial
+// sum, and every block adds all partials in the same fixed order (double-buffered by step).
+template <int KP>
+__global__ void __launch_bounds__(kThreads) k_arnoldi_mgs(int n, int K, int j, int m, double rtol,
+                                                          const double* __restrict__ V, long vstride, double* w,
+                                                          double* partial, ArnoldiState st) {
+    cg::grid_group grid = cg::this_grid();
+    constexpr int RPB = kThreads / KP;
+    __shared__ double red[kThreads / 32][KP];
+    __shared__ double hsh[KP];
+    __shared__ int any;
+    const int q = threadIdx.x % KP;
+    const bool qa = q < K;
+    const long r0 = (long)blockIdx.x * RPB + threadIdx.x / KP;
+    const long rs = (long)gridDim.x * RPB;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nb = gridDim.x;
+    // sum over the grid of each thread's acc for its right-hand side; the result lands in hsh[q]
+    auto reduce_all = [&](double acc, int buf) {
+#pragma unroll
+        for (int o = 16; o >= KP; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane < KP) red[warp][lane] = acc;
+        __syncthreads();
+        if (threadIdx.x < KP) {
+            double s = 0.0;
+            for (int wi = 0; wi < kThreads / 32; ++wi) s += red[wi][threadIdx.x];
+            partial[((long)buf * nb + blockIdx.x) * KP + threadIdx.x] = s;
+        }
+        grid.sync();
+        if (warp == 0) {
+            for (int qq = 0; qq < KP; ++qq) {
+                double s = 0.0;
+                for (int b = lane; b < nb; b += 32) s += partial[((long)buf * nb + b) * KP + qq];
+#pragma unroll
+                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) hsh[qq] = s;
+            }
+        }
+        __syncthreads();
+    };
+    for (int a = 0; a <= j; ++a) {
+        const double* va = V + (long)a * vstride;
+        double acc = 0.0;
+        if (qa)
+            for (long r = r0; r < n; r += rs) acc = fma(va[r * K + q], w[r * K + q], acc);
+        reduce_all(acc, a & 1);
+        const double h = hsh[q];
+        if (blockIdx.x == 0 && threadIdx.x < K) st.h1[a * K + threadIdx.x] = hsh[threadIdx.x];
+        if (qa)
+            for (long r = r0; r < n; r += rs) w[r * K + q] = fma(-h, va[r * K + q], w[r * K + q]);
+    }
+    double acc = 0.0;
+    if (qa)
+        for (long r = r0; r < n; r += rs) acc = fma(w[r * K + q], w[r * K + q], acc);
+    reduce_all(acc, (j + 1) & 1);
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) any = 0;
+        __syncthreads();
+        if (threadIdx.x < K) {
+            const bool live = arnoldi_column(st, K, j, m, rtol, threadIdx.x, sqrt(fmax(hsh[threadIdx.x], 0.0)));
+            if (live) atomicOr(&any, 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *st.any = any;
+    }
+    grid.sync();
+    const double f = qa ? st.f[q] : 0.0;
+    if (qa)
+        for (long r = r0; r < n; r += rs) w[r * K + q] *= f;
+}
+
+// y = R^-1 g on each right-hand side's rotated Hessenberg; zero beyond its column count
+__global__ void k_backsolve(int K, int m, ArnoldiState st) {
+    const int q = threadIdx.x;
+    if (q >= K) return;
+    const int jj = st.jq[q];
+    for (int a = m - 1; a >= jj; --a) st.y[a * K + q] = 0.0;
+    for (int a = jj - 1; a >= 0; --a) {
+        double s = st.g[a * K + q];
+        for (int c = a + 1; c < jj; ++c) s -= st.H[((size_t)a * m + c) * K + q] * st.y[c * K + q];
+        const double d = st.H[((size_t)a * m + a) * K + q];
+        st.y[a * K + q] = d != 0.0 ? s / d : 0.0;
+    }
+}
+
 int grid_for(long total) { return (int)std::max(1L, std::min((long)num_sms() * 8, (total + kThreads - 1) / kThreads)); }
 
-// Dots <V_a, w> for a < count, per right-hand side, into dev_out[count][K].
 struct Dots {
     double* partial = nullptr;
     int nblk = 0;
-    int cap = 0;
     hec_status init(int maxcount, int K) {
         nblk = num_sms() * 2;
-        cap = maxcount;
         return dalloc(&partial, (size_t)maxcount * nblk * K);
     }
     ~Dots() { cudaFree(partial); }
     template <int KP>
-    hec_status run_kp(int n, int K, const double* V, long vstride, int count, const double* w, double* out, bool acc,
-                      cudaStream_t s) {
-        dim3 g(nblk, (count + kDotGroup - 1) / kDotGroup);
-        k_multidot<KP><<<g, kThreads, 0, s>>>(n, K, V, vstride, count, w, partial);
-        count_launch();
-        k_reduce<<<(count * K + 127) / 128, 128, 0, s>>>(count, nblk, K, partial, out, acc ? 1 : 0);
-        HEC_LAUNCHED();
+    void run_kp(int n, int K, const double* V, long vstride, int count, int self, const double* w, double* out,
+                const int* gate, cudaStream_t s) {
+        const int total = count + self;
+        dim3 g(nblk, (total + kDotGroup - 1) / kDotGroup);
+        {
+            ProfScope ps_(s, PROF_GS);
+            k_multidot<KP><<<g, kThreads, 0, s>>>(n, K, V, vstride, count, self, w, partial, gate);
+        }
+        {
+            ProfScope ps_(s, PROF_GS);
+            k_reduce<<<(total * K * 32 + 255) / 256, 256, 0, s>>>(total, nblk, K, partial, out, gate);
+        }
+        count_launch(2);
+    }
+    hec_status run(int n, int K, const double* V, long vstride, int count, int self, const double* w, double* out,
+                   const int* gate, cudaStream_t s) {
+        if (K <= 1) run_kp<1>(n, K, V, vstride, count, self, w, out, gate, s);
+        else if (K <= 2) run_kp<2>(n, K, V, vstride, count, self, w, out, gate, s);
+        else if (K <= 4) run_kp<4>(n, K, V, vstride, count, self, w, out, gate, s);
+        else if (K <= 8) run_kp<8>(n, K, V, vstride, count, self, w, out, gate, s);
+        else run_kp<16>(n, K, V, vstride, count, self, w, out, gate, s);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_error(e, "multidot");
         return HEC_OK;
     }
-    hec_status run(int n, int K, const double* V, long vstride, int count, const double* w, double* out, bool acc,
-                   cudaStream_t s) {
-        if (K <= 1) return run_kp<1>(n, K, V, vstride, count, w, out, acc, s);
-        if (K <= 2) return run_kp<2>(n, K, V, vstride, count, w, out, acc, s);
-        if (K <= 4) return run_kp<4>(n, K, V, vstride, count, w, out, acc, s);
-        if (K <= 8) return run_kp<8>(n, K, V, vstride, count, w, out, acc, s);
-        return run_kp<16>(n, K, V, vstride, count, w, out, acc, s);
+};
+
+// Launcher of the persistent Arnoldi kernel: grid = resident blocks (cooperative launch).
+struct Mgs {
+    double* partial = nullptr;
+    int cap_blocks = 0;
+    hec_status init() {
+        cap_blocks = num_sms() * (2048 / kThreads);
+        return dalloc(&partial, (size_t)2 * cap_blocks * 16);
+    }
+    ~Mgs() { cudaFree(partial); }
+    template <int KP>
+    hec_status run_kp(int n, int K, int j, int m, double rtol, const double* V, long vstride, double* w,
+                      ArnoldiState& st, cudaStream_t s) {
+        const void* k = (const void*)k_arnoldi_mgs<KP>;
+        static int per_sm = -1;  // per template instance
+        if (per_sm < 0) per_sm = max_coop_blocks(k, kThreads, 0);
+        if (per_sm <= 0) return set_error(HEC_ERR_CUDA, "Arnoldi kernel cannot be resident");
+        const long want = ((long)n * KP + kThreads - 1) / kThreads;
+        int blocks = (int)std::max(1L, std::min<long>(std::min(per_sm * num_sms(), cap_blocks), want));
+        double* part = partial;
+        void* args[] = {&n, &K, &j, &m, &rtol, (void*)&V, &vstride, &w, &part, &st};
+        ProfScope ps_(s, PROF_GS);
+        HEC_CUDA(cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(kThreads), args, 0, s));
+        count_launch();
+        return HEC_OK;
+    }
+    hec_status run(int n, int K, int j, int m, double rtol, const double* V, long vstride, double* w,
+                   ArnoldiState& st, cudaStream_t s) {
+        if (K <= 1) return run_kp<1>(n, K, j, m, rtol, V, vstride, w, st, s);
+        if (K <= 2) return run_kp<2>(n, K, j, m, rtol, V, vstride, w, st, s);
+        if (K <= 4) return run_kp<4>(n, K, j, m, rtol, V, vstride, w, st, s);
+        if (K <= 8) return run_kp<8>(n, K, j, m, rtol, V, vstride, w, st, s);
+        return run_kp<16>(n, K, j, m, rtol, V, vstride, w, st, s);
     }
 };
 
@@ -174,8 +375,11 @@ hec_status spmv_impl(const hec_matrix* A, int K, double alpha, const double* x, 
     auto go = [&](auto kp) -> hec_status {
         constexpr int KP = decltype(kp)::value;
         int blocks = (int)(((long)A->n * KP + kThreads - 1) / kThreads);
-        k_spmv<KP><<<blocks, kThreads, 0, s>>>(A->n, A->ld, A->w, A->ell_col, (const double*)A->ell_val, A->tptr,
-                                               A->tcol, (const double*)A->tval, K, alpha, x, ldx, beta, y, ldy);
+        {
+            ProfScope ps_(s, PROF_SPMV);
+            k_spmv<KP><<<blocks, kThreads, 0, s>>>(A->n, A->ld, A->w, A->ell_col, (const double*)A->ell_val, A->tptr,
+                                                   A->tcol, (const double*)A->tval, K, alpha, x, ldx, beta, y, ldy);
+        }
         HEC_LAUNCHED();
         return HEC_OK;
     };
@@ -199,6 +403,27 @@ HEC_API hec_status spmv(const hec_matrix* A, int nrhs, double alpha, const doubl
     return spmv_impl(A, nrhs, alpha, x, ldx, beta, y, ldy, S(stream));
 }
 
+namespace {
+// Device and pinned workspace of one fgmres_solve call.
+struct FgmresWork {
+    double* V = nullptr;       // (m+1) blocks of n x K
+    double* Z = nullptr;       // m blocks of n x K
+    double* small = nullptr;   // Arnoldi arrays
+    int* ints = nullptr;
+    int* pinned = nullptr;     // host ring of per-iteration "any active" flags
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    ~FgmresWork() {
+        cudaFree(V);
+        cudaFree(Z);
+        cudaFree(small);
+        cudaFree(ints);
+        if (pinned) cudaFreeHost(pinned);
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+}  // namespace
+
 HEC_API hec_status fgmres_solve(const hec_matrix* A, const ilu_precond* M, int nrhs, const double* b, int ldb,
                                 double* x, int ldx, int restart, double rtol, int max_iters, hec_fgmres_info* info,
                                 void* stream) {
@@ -216,158 +441,142 @@ HEC_API hec_status fgmres_solve(const hec_matrix* A, const ilu_precond* M, int n
         if (info) *info = inf;
         return HEC_OK;
     }
-    double *V = nullptr, *Z = nullptr, *dh = nullptr, *dsc = nullptr;
-    hec_status st = HEC_OK;
+    FgmresWork W;
     Dots dots;
-    if ((st = dalloc(&V, (size_t)(m + 1) * nk)) || (st = dalloc(&Z, (size_t)m * nk)) ||
-        (st = dalloc(&dh, (size_t)(2 * (m + 1) + 4) * K)) || (st = dots.init(m + 1, K))) {
-        cudaFree(V); cudaFree(Z); cudaFree(dh);
+    Mgs mgs;
+    const size_t nsmall = (size_t)K * ((size_t)(m + 1) * m + 2 * m + (m + 1) + m + (m + 2) + (m + 1) + 4);
+    hec_status st = HEC_OK;
+    if ((st = dalloc(&W.V, (size_t)(m + 1) * nk)) || (st = dalloc(&W.Z, (size_t)m * nk)) ||
+        (st = dalloc(&W.small, nsmall)) || (st = dalloc(&W.ints, (size_t)2 * K + 2)) || (st = dots.init(m + 2, K)) ||
+        (st = mgs.init()))
         return st;
+    HEC_CUDA(cudaHostAlloc((void**)&W.pinned, 2 * sizeof(int), cudaHostAllocDefault));
+    HEC_CUDA(cudaEventCreateWithFlags(&W.ev[0], cudaEventDisableTiming));
+    HEC_CUDA(cudaEventCreateWithFlags(&W.ev[1], cudaEventDisableTiming));
+    ArnoldiState as;
+    {
+        double* p = W.small;
+        as.H = p; p += (size_t)(m + 1) * m * K;
+        as.cs = p; p += (size_t)m * K;
+        as.sn = p; p += (size_t)m * K;
+        as.g = p; p += (size_t)(m + 1) * K;
+        as.y = p; p += (size_t)m * K;
+        as.h1 = p; p += (size_t)(m + 2) * K;
+        as.h2 = p; p += (size_t)(m + 1) * K;
+        as.n1 = p; p += K;
+        as.n2 = p; p += K;
+        as.f = p; p += K;
+        as.bnorm = p; p += K;
+        as.active = W.ints;
+        as.jq = W.ints + K;
+        as.reorth = W.ints + 2 * K;
+        as.any = W.ints + 2 * K + 1;
     }
-    double* dh2 = dh + (size_t)(m + 1) * K;  // second Gram-Schmidt pass
-    dsc = dh2 + (size_t)(m + 1) * K;         // [K] scale factors, [K] norms
-    double* dnorm = dsc + K;
-    std::vector<double> H((size_t)(m + 1) * m * K), cs((size_t)m * K), sn((size_t)m * K), g((size_t)(m + 1) * K);
-    std::vector<double> bnorm(K), hcol((size_t)(m + 1) * K), nrm(K), yv((size_t)m * K), f(K);
-    std::vector<int> jq(K), conv(K, 0);
     const int gb = grid_for(nk);
-    auto fail = [&](hec_status e) {
-        cudaFree(V); cudaFree(Z); cudaFree(dh);
-        return e;
-    };
-    auto norms = [&](const double* v, double* host) -> hec_status {
-        HEC_CHECK(dots.run(n, K, v, nk, 1, v, dnorm, false, s));
-        HEC_CUDA(cudaMemcpyAsync(host, dnorm, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
-        HEC_CUDA(cudaStreamSynchronize(s));
-        for (int q = 0; q < K; ++q) host[q] = std::sqrt(std::max(host[q], 0.0));
-        return HEC_OK;
-    };
+    std::vector<double> hb(K), hn(K), g0((size_t)(m + 1) * K), fh(K);
+    std::vector<int> act(K), jq(K);
+    // ||b||
+    {
+        ProfScope ps_(s, PROF_VEC);
+        k_copy<<<gb, kThreads, 0, s>>>(nk, K, b, ldb, W.V, K);
+    }
+    count_launch();
+    HEC_CHECK(dots.run(n, K, W.V, nk, 0, 1, W.V, as.n1, nullptr, s));
+    HEC_CUDA(cudaMemcpyAsync(hb.data(), as.n1, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+    HEC_CUDA(cudaStreamSynchronize(s));
+    for (int q = 0; q < K; ++q) hb[q] = std::sqrt(std::max(hb[q], 0.0));
+    HEC_CUDA(cudaMemcpyAsync(as.bnorm, hb.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s));
+    int its = 0, restarts = 0;
+    double worst = 0.0;
+    bool all_conv = false;
     auto check_sweeps = [&]() -> hec_status {
         if (!M) return HEC_OK;
         hec_status a = hec_sync_status(M->L, stream);
         hec_status c = hec_sync_status(M->U, stream);
         return a != HEC_OK ? a : c;
     };
-    // ||b||
-    k_copy<<<gb, kThreads, 0, s>>>(nk, K, b, ldb, V, K);
-    count_launch();
-    if ((st = norms(V, bnorm.data()))) return fail(st);
-    int its = 0, restarts = 0;
-    double worst = 0.0;
-    bool all_conv = false;
     while (true) {
-        // r = b - A x, beta = ||r||, v_0 = r / beta
-        k_copy<<<gb, kThreads, 0, s>>>(nk, K, b, ldb, V, K);
-        count_launch();
-        // V currently holds b; subtract A x (x may have a leading dimension != K)
-        if (ldx == K) {
-            if ((st = spmv_impl(A, K, -1.0, x, ldx, 1.0, V, K, s))) return fail(st);
-        } else {
-            if ((st = spmv_impl(A, K, -1.0, x, ldx, 1.0, V, K, s))) return fail(st);
+        // r = b - A x; beta = ||r||; v_0 = r / beta (host decides on the restart)
+        {
+            ProfScope ps_(s, PROF_VEC);
+            k_copy<<<gb, kThreads, 0, s>>>(nk, K, b, ldb, W.V, K);
         }
-        if ((st = norms(V, nrm.data()))) return fail(st);
+        count_launch();
+        HEC_CHECK(spmv_impl(A, K, -1.0, x, ldx, 1.0, W.V, K, s));
+        HEC_CHECK(dots.run(n, K, W.V, nk, 0, 1, W.V, as.n1, nullptr, s));
+        HEC_CUDA(cudaMemcpyAsync(hn.data(), as.n1, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+        HEC_CUDA(cudaStreamSynchronize(s));
+        HEC_CHECK(check_sweeps());
         all_conv = true;
         worst = 0.0;
+        std::fill(g0.begin(), g0.end(), 0.0);
         for (int q = 0; q < K; ++q) {
-            double rel = bnorm[q] > 0 ? nrm[q] / bnorm[q] : 0.0;
+            const double beta = std::sqrt(std::max(hn[q], 0.0));
+            const double rel = hb[q] > 0 ? beta / hb[q] : 0.0;
             worst = std::max(worst, rel);
-            conv[q] = rel <= rtol;
-            all_conv = all_conv && conv[q];
-            f[q] = nrm[q] > 0 ? 1.0 / nrm[q] : 0.0;
-            std::fill(&g[0] + 0, &g[0] + 0, 0.0);
-            for (int a = 0; a <= m; ++a) g[(size_t)a * K + q] = 0.0;
-            g[q] = nrm[q];
+            const bool c = rel <= rtol;
+            all_conv = all_conv && c;
+            act[q] = c ? 0 : 1;
+            fh[q] = beta > 0 ? 1.0 / beta : 0.0;
+            g0[q] = beta;
             jq[q] = 0;
         }
         if (all_conv || its >= max_iters) break;
-        HEC_CUDA(cudaMemcpyAsync(dsc, f.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s));
-        k_scale<<<gb, kThreads, 0, s>>>(nk, K, V, dsc);
+        HEC_CUDA(cudaMemcpyAsync(as.g, g0.data(), sizeof(double) * (m + 1) * K, cudaMemcpyHostToDevice, s));
+        HEC_CUDA(cudaMemcpyAsync(as.f, fh.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s));
+        HEC_CUDA(cudaMemcpyAsync(as.active, act.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
+        HEC_CUDA(cudaMemcpyAsync(as.jq, jq.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
+        {
+            ProfScope ps_(s, PROF_VEC);
+            k_scale<<<gb, kThreads, 0, s>>>(nk, K, W.V, as.f);
+        }
         count_launch();
-        std::vector<int> active(K);
-        for (int q = 0; q < K; ++q) active[q] = !conv[q];
-        int j = 0;
-        for (; j < m && its < max_iters; ++j) {
-            double* vj = V + (long)j * nk;
-            double* zj = Z + (long)j * nk;
-            double* wv = V + (long)(j + 1) * nk;
+        const int jlimit = std::min(m, max_iters - its);
+        int launched = 0;
+        for (int j = 0; j < jlimit; ++j) {
+            double* vj = W.V + (long)j * nk;
+            double* zj = W.Z + (long)j * nk;
+            double* wv = W.V + (long)(j + 1) * nk;
             if (M) {
-                if ((st = ilu_apply(M, K, vj, K, zj, K, stream))) return fail(st);
+                HEC_CHECK(ilu_apply(M, K, vj, K, zj, K, stream));
             } else {
                 HEC_CUDA(cudaMemcpyAsync(zj, vj, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
             }
-            if ((st = spmv_impl(A, K, 1.0, zj, K, 0.0, wv, K, s))) return fail(st);
-            // classical Gram-Schmidt, twice
-            if ((st = dots.run(n, K, V, nk, j + 1, wv, dh, false, s))) return fail(st);
-            k_cgs_update<<<gb, kThreads, 0, s>>>(nk, K, V, nk, j + 1, dh, wv);
-            count_launch();
-            if ((st = dots.run(n, K, V, nk, j + 1, wv, dh2, false, s))) return fail(st);
-            k_cgs_update<<<gb, kThreads, 0, s>>>(nk, K, V, nk, j + 1, dh2, wv);
-            count_launch();
-            HEC_CUDA(cudaMemcpyAsync(hcol.data(), dh, sizeof(double) * (j + 1) * K, cudaMemcpyDeviceToHost, s));
-            std::vector<double> h2((size_t)(j + 1) * K);
-            HEC_CUDA(cudaMemcpyAsync(h2.data(), dh2, sizeof(double) * (j + 1) * K, cudaMemcpyDeviceToHost, s));
-            if ((st = norms(wv, nrm.data()))) return fail(st);
-            its++;
-            bool any_active = false;
-            for (int q = 0; q < K; ++q) {
-                f[q] = 0.0;
-                if (!active[q]) continue;
-                for (int a = 0; a <= j; ++a) H[((size_t)a * m + j) * K + q] = hcol[a * K + q] + h2[a * K + q];
-                double hn = nrm[q];
-                H[((size_t)(j + 1) * m + j) * K + q] = hn;
-                f[q] = hn > 0 ? 1.0 / hn : 0.0;
-                for (int a = 0; a < j; ++a) {
-                    double h0 = H[((size_t)a * m + j) * K + q], h1 = H[((size_t)(a + 1) * m + j) * K + q];
-                    H[((size_t)a * m + j) * K + q] = cs[a * K + q] * h0 + sn[a * K + q] * h1;
-                    H[((size_t)(a + 1) * m + j) * K + q] = -sn[a * K + q] * h0 + cs[a * K + q] * h1;
-                }
-                double h0 = H[((size_t)j * m + j) * K + q], h1 = hn;
-                double den = std::sqrt(h0 * h0 + h1 * h1);
-                double c = den == 0.0 ? 1.0 : h0 / den, sv = den == 0.0 ? 0.0 : h1 / den;
-                cs[j * K + q] = c;
-                sn[j * K + q] = sv;
-                H[((size_t)j * m + j) * K + q] = c * h0 + sv * h1;
-                double gj = g[(size_t)j * K + q];
-                g[(size_t)(j + 1) * K + q] = -sv * gj;
-                g[(size_t)j * K + q] = c * gj;
-                jq[q] = j + 1;
-                if (std::fabs(g[(size_t)(j + 1) * K + q]) <= rtol * bnorm[q] || hn == 0.0) active[q] = 0;
-                else any_active = true;
-            }
-            if (!any_active) { j++; break; }
-            HEC_CUDA(cudaMemcpyAsync(dsc, f.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s));
-            k_scale<<<gb, kThreads, 0, s>>>(nk, K, wv, dsc);
-            count_launch();
-        }
-        // back substitution on the rotated Hessenberg, x += Z y
-        std::fill(yv.begin(), yv.end(), 0.0);
-        int jmax = 0;
-        for (int q = 0; q < K; ++q) {
-            int jj = jq[q];
-            jmax = std::max(jmax, jj);
-            for (int a = jj - 1; a >= 0; --a) {
-                double sacc = g[(size_t)a * K + q];
-                for (int c = a + 1; c < jj; ++c) sacc -= H[((size_t)a * m + c) * K + q] * yv[c * K + q];
-                double d = H[((size_t)a * m + a) * K + q];
-                yv[a * K + q] = d != 0.0 ? sacc / d : 0.0;
+            HEC_CHECK(spmv_impl(A, K, 1.0, zj, K, 0.0, wv, K, s));
+            // modified Gram-Schmidt, ||w||, Hessenberg column, rotations, w /= h_{j+1,j}
+            HEC_CHECK(mgs.run(n, K, j, m, rtol, W.V, nk, wv, as, s));
+            HEC_CUDA(cudaMemcpyAsync(W.pinned + (j & 1), as.any, sizeof(int), cudaMemcpyDeviceToHost, s));
+            HEC_CUDA(cudaEventRecord(W.ev[j & 1], s));
+            launched = j + 1;
+            // stay at most one iteration ahead: look at the previous iteration's flag
+            if (j >= 1) {
+                HEC_CUDA(cudaEventSynchronize(W.ev[(j - 1) & 1]));
+                if (W.pinned[(j - 1) & 1] == 0) break;  // every right-hand side finished at j-1
             }
         }
-        if (jmax > 0) {
-            HEC_CUDA(cudaMemcpyAsync(dh, yv.data(), sizeof(double) * jmax * K, cudaMemcpyHostToDevice, s));
-            k_update_x<<<gb, kThreads, 0, s>>>(nk, K, Z, nk, jmax, dh, x, ldx);
-            count_launch();
+        // y = R^-1 g, x += Z y
+        {
+            ProfScope ps_(s, PROF_ARNOLDI);
+            k_backsolve<<<1, 32, 0, s>>>(K, m, as);
         }
+        {
+            ProfScope ps_(s, PROF_VEC);
+            k_update_x<<<gb, kThreads, 0, s>>>(nk, K, W.Z, nk, launched, as.y, x, ldx);
+        }
+        count_launch(2);
+        HEC_CUDA(cudaMemcpyAsync(jq.data(), as.jq, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
+        HEC_CUDA(cudaStreamSynchronize(s));
+        its += *std::max_element(jq.begin(), jq.end());
         restarts++;
-        if ((st = check_sweeps())) return fail(st);
+        HEC_CUDA(cudaGetLastError());
     }
-    if ((st = check_sweeps())) return fail(st);
+    HEC_CHECK(check_sweeps());
     inf.iterations = its;
     inf.restarts = restarts;
     inf.converged = all_conv ? 1 : 0;
     inf.rel_residual = worst;
     inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (info) *info = inf;
-    cudaFree(V); cudaFree(Z); cudaFree(dh);
     if (!all_conv) return set_error(HEC_ERR_NOT_CONVERGED, "fgmres_solve: max_iters reached before rtol");
     return HEC_OK;
 }

@@ -286,7 +286,10 @@ hec_status launch_sweep(const sptrsv_plan* pl, SweepParams& sp, cudaStream_t s) 
     int blocks = (int)std::max(1L, std::min((long)per_sm * num_sms(), want));
     long count = (long)sp.n * sp.K;
     int fb = (int)std::min(4096L, std::max(1L, (count + 255) / 256));
-    k_fill_sentinel<XT><<<fb, 256, 0, s>>>((XT*)sp.xp, count);
+    {
+        ProfScope ps_(s, PROF_FILL);
+        k_fill_sentinel<XT><<<fb, 256, 0, s>>>((XT*)sp.xp, count);
+    }
     HEC_LAUNCHED();
     void* args[] = {&sp};
     void* tok = nullptr;

@@ -124,11 +124,25 @@ def profile_enable(on=True):
     _check(_hec_profile_enable(1 if on else 0), "hec_profile_enable")
 
 
+_hec_profile_read_category = _sig("hec_profile_read_category", _i, ctypes.POINTER(_d), ctypes.POINTER(_ll))
+PROFILE_CATEGORIES = ["sweep", "spmv", "gram_schmidt", "arnoldi", "vector", "fill"]
+
+
 def profile_read(reset=True):
     """(summed device ms, launches) of the sweep kernels recorded since the last reset."""
     ms, n = _d(), _ll()
     _check(_hec_profile_read(ctypes.byref(ms), ctypes.byref(n), 1 if reset else 0), "hec_profile_read")
     return ms.value, n.value
+
+
+def profile_breakdown():
+    """{category: (device ms, launches)} recorded since the last reset (read before profile_read)."""
+    out = {}
+    for i, name in enumerate(PROFILE_CATEGORIES):
+        ms, n = _d(), _ll()
+        _check(_hec_profile_read_category(i, ctypes.byref(ms), ctypes.byref(n)), "hec_profile_read_category")
+        out[name] = (ms.value, n.value)
+    return out
 
 
 def version():
