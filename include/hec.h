@@ -271,8 +271,8 @@ hec_status ilu_factor(int n, const int* rowptr, const int* col, const double* va
  * sptrsv_noalloc_capacity() bytes (32 MiB), which every GPU that loads the library holds until
  * the process exits.  The caller still passes tri and lv (built once with sptrsv_analyze and
  * hec_from_csr) and the device arrays b and x, with the layout of sptrsv_lower.
- *   - Size limit: a problem whose scratch (n * nrhs * 8 bytes for FP64 factors, 4 for FP32 /
- *     BF16, plus the chunk table) exceeds the buffer is rejected with HEC_ERR_INVALID_ARG and a
+ *   - Size limit: a problem whose scratch (n * (nrhs + 1) * 8 bytes for FP64 factors, 4 for
+ *     FP32 / BF16, plus the chunk table) exceeds the buffer is rejected with HEC_ERR_INVALID_ARG and a
  *     message giving the bytes needed; use sptrsv_lower / sptrsv_upper for those.
  *   - The first call on a device looks up the buffer's device address (cudaGetSymbolAddress)
  *     with that device current; make that first call before any stream capture.

@@ -102,6 +102,7 @@ struct sptrsv_plan {
     int* status = nullptr;     // device status word
     int2* chunks[5] = {};      // level-aligned chunk tables for 32, 16, 8, 4, 2 rows per warp step
     int nchunks[5] = {};
+    void* dinv = nullptr;      // reciprocal diagonal in the work type (NULL: the kernel divides)
 };
 
 struct ilu_precond {

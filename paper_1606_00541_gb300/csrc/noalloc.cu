@@ -89,6 +89,22 @@ __global__ void k_na_table(int nlev, const int* __restrict__ level_ptr, const in
     }
 }
 
+// reciprocal diagonal in the work type, the same arithmetic as a solve plan's
+template <typename VT, typename XT>
+__global__ void k_na_dinv(int n, const int* __restrict__ tptr, const VT* __restrict__ tval, XT* dinv) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const VT d = tval[tptr[r + 1] - 1];
+    if (sizeof(XT) == 8) dinv[r] = (XT)(1.0 / (double)d);
+    else dinv[r] = (XT)(1.0f / (float)d);
+}
+template <>
+__global__ void k_na_dinv<__nv_bfloat16, float>(int n, const int* __restrict__ tptr, const __nv_bfloat16* __restrict__ tval,
+                                                float* dinv) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) dinv[r] = 1.0f / __bfloat162float(tval[tptr[r + 1] - 1]);
+}
+
 hec_status scratch_ptr(unsigned char** out) {
     int dev = 0;
     HEC_CUDA(cudaGetDevice(&dev));
@@ -130,8 +146,10 @@ HEC_API hec_status sptrsv_solve_noalloc(const hec_matrix* tri, const hec_levels*
     const size_t off_cptr = 256;
     const size_t off_tbl = off_cptr + align256(sizeof(int) * ((size_t)nlev + 1));
     const size_t off_xp = off_tbl + align256(sizeof(int2) * chunk_cap);
-    const size_t xp_bytes = (tri->vdt == HEC_F64 ? 8 : 4) * (size_t)n * nrhs;
-    const size_t need = off_xp + align256(xp_bytes);
+    const size_t ws = tri->vdt == HEC_F64 ? 8 : 4;
+    const size_t xp_bytes = ws * (size_t)n * nrhs;
+    const size_t off_dinv = off_xp + align256(xp_bytes);
+    const size_t need = off_dinv + align256(ws * (size_t)n);
     if (need > kScratchBytes)
         return set_error(HEC_ERR_INVALID_ARG,
                          "sptrsv_solve_noalloc: problem needs " + std::to_string(need) + " bytes of scratch, more than the " +
@@ -150,6 +168,15 @@ HEC_API hec_status sptrsv_solve_noalloc(const hec_matrix* tri, const hec_levels*
     const int tb = (int)std::min<size_t>(4096, (chunk_cap + 255) / 256);
     k_na_table<<<tb, 256, 0, s>>>(nlev, lv->level_ptr, cptr, rpw, (int)chunk_cap, tbl);
     HEC_LAUNCHED();
+    void* dinv = base + off_dinv;
+    const int gd = (n + 255) / 256;
+    if (tri->vdt == HEC_F64)
+        k_na_dinv<double, double><<<gd, 256, 0, s>>>(n, tri->tptr, (const double*)tri->tval, (double*)dinv);
+    else if (tri->vdt == HEC_F32)
+        k_na_dinv<float, float><<<gd, 256, 0, s>>>(n, tri->tptr, (const float*)tri->tval, (float*)dinv);
+    else
+        k_na_dinv<__nv_bfloat16, float><<<gd, 256, 0, s>>>(n, tri->tptr, (const __nv_bfloat16*)tri->tval, (float*)dinv);
+    HEC_LAUNCHED();
     // a plan that lives on the host stack and points into the static scratch
     sptrsv_plan plan;
     plan.T = tri;
@@ -159,6 +186,7 @@ HEC_API hec_status sptrsv_solve_noalloc(const hec_matrix* tri, const hec_levels*
     plan.status = status;
     plan.chunks[kp_idx] = tbl;
     plan.nchunks[kp_idx] = (int)chunk_cap;
+    plan.dinv = dinv;
     hec_status st = sweep(&plan, nrhs, b, ldb, lv->iperm, x, ldx, lv->iperm, s);
     if (st != HEC_OK) return st;
     if (status_out) {

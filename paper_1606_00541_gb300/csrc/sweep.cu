@@ -44,6 +44,7 @@ struct SweepParams {
     int backoff_ns;
     const int2* __restrict__ chunks;  // (first row, rows) of each level-aligned chunk
     int nchunks;
+    const void* __restrict__ dinv;     // reciprocal diagonal in the work type (NULL: divide)
 };
 
 template <typename XT> struct Acc { typedef float T; };
@@ -196,7 +197,9 @@ __global__ void __launch_bounds__(256) k_sweep(SweepParams p) {
             t0 = __ldg(p.tptr + r);
             const int t1 = __ldg(p.tptr + r + 1) - 1;
             tl = t1 - t0;
-            diag = ldv<VT, AT>(tv + t1);  // the diagonal is the last tail entry
+            // the diagonal is the last tail entry; with a precomputed reciprocal the division
+            // leaves the critical path (one multiply after the last dependency arrives)
+            diag = p.dinv ? (AT)__ldg((const XT*)p.dinv + r) : ldv<VT, AT>(tv + t1);
             sr = p.scatter ? __ldg(p.scatter + r) : r;
         }
         DepBatch<XT, AT, WMAX> slab;
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepParams p) {
             acc = tail.accumulate(acc);
         }
         if (act) {
-            const AT xr = acc / diag;
+            const AT xr = p.dinv ? acc * diag : acc / diag;
             if (r != p.skip_row) publish_x(xp + (long)r * K + q, (XT)xr);
             if (sr >= 0) p.x[(long)sr * p.ldx + q] = (double)xr;
         }
@@ -317,6 +320,27 @@ hec_status dispatch_w(const sptrsv_plan* pl, SweepParams& sp, cudaStream_t s) {
 }
 
 size_t work_size(hec_dtype d) { return d == HEC_F64 ? 8 : 4; }
+
+// dinv[r] = 1 / diagonal of new row r, in the work type (FP64 for FP64 factors, else FP32)
+template <typename VT, typename XT>
+__global__ void k_dinv(int n, const int* __restrict__ tptr, const VT* __restrict__ tval, XT* dinv) {
+    typedef typename Acc<XT>::T AT;
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) dinv[r] = (XT)(AT(1) / ldv<VT, AT>(tval + tptr[r + 1] - 1));
+}
+
+hec_status build_dinv(sptrsv_plan* p) {
+    const hec_matrix* T = p->T;
+    HEC_CHECK(dmalloc(&p->dinv, work_size(T->vdt) * (size_t)T->n + 16));
+    if (T->n == 0) return HEC_OK;
+    const int g = (T->n + 255) / 256;
+    if (T->vdt == HEC_F64) k_dinv<double, double><<<g, 256>>>(T->n, T->tptr, (const double*)T->tval, (double*)p->dinv);
+    else if (T->vdt == HEC_F32) k_dinv<float, float><<<g, 256>>>(T->n, T->tptr, (const float*)T->tval, (float*)p->dinv);
+    else k_dinv<__nv_bfloat16, float><<<g, 256>>>(T->n, T->tptr, (const __nv_bfloat16*)T->tval, (float*)p->dinv);
+    HEC_LAUNCHED();
+    HEC_CUDA(cudaStreamSynchronize(0));
+    return HEC_OK;
+}
 
 // Level-aligned chunks of at most rpw rows: level l contributes ceil(N_l / rpw) chunks.
 __global__ void k_chunk_counts(int nlev, const int* __restrict__ level_ptr, int rpw, int* cnt) {
@@ -398,6 +422,7 @@ hec_status sweep(const sptrsv_plan* pl, int nrhs, const double* b, int ldb, cons
     sp.budget = pl->wait_cycles;
     sp.skip_row = pl->skip_row;
     sp.backoff_ns = pl->backoff_ns;
+    sp.dinv = pl->dinv;
     switch (T->vdt) {
         case HEC_F64: return dispatch_w<double, double>(pl, sp, s);
         case HEC_F32: return dispatch_w<float, float>(pl, sp, s);
@@ -424,6 +449,7 @@ void free_plan(sptrsv_plan* p) {
     cudaFree(p->xp);
     cudaFree(p->status);
     for (int i = 0; i < 5; ++i) cudaFree(p->chunks[i]);
+    cudaFree(p->dinv);
     delete p;
 }
 
@@ -457,6 +483,7 @@ HEC_API hec_status sptrsv_plan_create(const hec_matrix* tri, const hec_levels* l
     if (st == HEC_OK) st = dalloc(&p->status, 1);
     if (st == HEC_OK && cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) st = cuda_error(cudaGetLastError(), "memset");
     if (st == HEC_OK) st = build_chunks(p);
+    if (st == HEC_OK) st = build_dinv(p);
     if (st != HEC_OK) { free_plan(p); return st; }
     *out = p;
     return HEC_OK;
