@@ -184,6 +184,15 @@ hec_status sptrsv_lower(const sptrsv_plan* p, int nrhs, const double* b, int ldb
 hec_status sptrsv_upper(const sptrsv_plan* p, int nrhs, const double* b, int ldb, double* x,
                         int ldx, void* stream);
 
+/* Autotuner: times the plan's own sweep (on a zero right-hand side, nrhs columns) for the
+ * candidate launch shapes block_threads in {128, 256} x blocks_per_sm in {2, 4, 8, 16} (those that
+ * fit 2048 threads per SM) and stores the fastest in the plan; `out` (host, may be NULL) receives
+ * it.  Results are cached per (rows, slab width, tail entries, levels, value type, nrhs rounded up
+ * to a power of two) for the life of the process.  Synchronizes `stream`.  The point-to-point
+ * sweep has no per-level barriers, so the paper's level-merging threshold has no counterpart;
+ * residency is the parameter that matters. */
+hec_status sptrsv_autotune(sptrsv_plan* p, int nrhs, hec_tune* out, void* stream);
+
 /* Reads and clears the device status word of a plan (synchronizes `stream`).  Returns HEC_OK,
  * HEC_ERR_TIMEOUT or HEC_ERR_OUT_OF_BOUNDS as recorded by the kernels since the last call. */
 hec_status hec_sync_status(const sptrsv_plan* p, void* stream);
@@ -257,6 +266,29 @@ hec_status hec_csr_destroy(hec_csr* M);
  * a nonzero diagonal in every row; ZERO_PIVOT if an eliminated pivot is zero.  Synchronizes. */
 hec_status ilu_factor(int n, const int* rowptr, const int* col, const double* val, int k,
                       hec_csr** L, hec_csr** U, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Restricted Additive Schwarz setup (Sec. 3; Eq. 4: the subdomain problems as one            */
+/* block-diagonal system)                                                                     */
+/* ---------------------------------------------------------------------------------------- */
+
+typedef struct hec_ras hec_ras;
+
+/* Builds the RAS subdomain system of A (n x n, CSR) for the ownership map part[n] (each row
+ * owned by one subdomain in [0, nsub); the paper partitions with METIS, the caller supplies any
+ * partition).  Overlap 1: subdomain s's extended set is its owned rows plus every column of an
+ * owned row, in ascending global index.  Outputs (owned by the handle, see hec_ras_get):
+ * ext_ptr[nsub+1] (extended rows of s are ext_ptr[s] .. ext_ptr[s+1]-1), ext2glob[n_ext] (global
+ * row of each extended row), owned[n_ext] (1 when the extended row is owned by its subdomain), and
+ * A_ext = diag(A_1, ..., A_s), A_s = A restricted to ext(s) x ext(s), as one block-diagonal CSR
+ * matrix in the extended numbering.  Factor A_ext with ilu_factor, then pass ext2glob and owned
+ * to ilu_create: ilu_apply then computes z = sum_s R0_s^T U_s^-1 L_s^-1 R_s r.  Requires
+ * nsub * n < 2^31.  Synchronizes `stream`. */
+hec_status ras_setup(int n, const int* rowptr, const int* col, const double* val, const int* part,
+                     int nsub, hec_ras** out, void* stream);
+hec_status hec_ras_get(const hec_ras* R, int* n_ext, const int** ext_ptr, const int** ext2glob,
+                       const unsigned char** owned, const hec_csr** A_ext);
+hec_status hec_ras_destroy(hec_ras* R);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Allocation-free sweep (the paper has no counterpart: this is a deployment convenience)      */

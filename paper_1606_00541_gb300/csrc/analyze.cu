@@ -251,6 +251,43 @@ hec_status compute_levels(int n, const int* rp, const int* col, int dep_side, he
     return st;
 }
 
+// Stable sort of (key, val) pairs by key, 0 <= key <= max_key, in place (LSD radix, 8-bit
+// digits).  Synchronizes.
+hec_status sort_pairs_i32(int* keys, int* vals, int n, int max_key, cudaStream_t s) {
+    if (n <= 1) return HEC_OK;
+    int *k1 = nullptr, *v1 = nullptr, *counts = nullptr;
+    const int ntiles = (n + kTileItems - 1) / kTileItems;
+    hec_status st = HEC_OK;
+    if ((st = dalloc(&k1, (size_t)n)) || (st = dalloc(&v1, (size_t)n)) ||
+        (st = dalloc(&counts, (size_t)kDigits * ntiles + 1))) {
+        cudaFree(k1); cudaFree(v1); cudaFree(counts);
+        return st;
+    }
+    int bits = 0;
+    while ((1LL << bits) <= (long long)max_key) bits++;
+    const int passes = std::max(1, (bits + kRadixBits - 1) / kRadixBits);
+    const int sblocks = (ntiles + kSortWarps - 1) / kSortWarps;
+    int *ka = keys, *va = vals, *kb = k1, *vb = v1;
+    for (int ps = 0; ps < passes && st == HEC_OK; ++ps) {
+        k_digit_count<<<sblocks, 32 * kSortWarps, 0, s>>>(n, ka, ps * kRadixBits, ntiles, counts);
+        count_launch();
+        st = exclusive_scan_i32(counts, counts, kDigits * ntiles, false, s);
+        if (st != HEC_OK) break;
+        k_digit_scatter<<<sblocks, 32 * kSortWarps, 0, s>>>(n, ka, va, ps * kRadixBits, ntiles, counts, kb, vb);
+        count_launch();
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (st == HEC_OK && ka != keys) {
+        cudaMemcpyAsync(keys, ka, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(vals, va, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (st == HEC_OK && e != cudaSuccess) st = cuda_error(e, "sort");
+    cudaFree(k1); cudaFree(v1); cudaFree(counts);
+    return st;
+}
+
 void free_levels(hec_levels* lv) {
     if (!lv) return;
     cudaFree(lv->level);

@@ -513,6 +513,94 @@ HEC_API hec_status sptrsv_upper(const sptrsv_plan* p, int nrhs, const double* b,
     return sweep_api(p, 1, nrhs, b, ldb, x, ldx, stream);
 }
 
+// ---- autotuner ------------------------------------------------------------------------------
+// Residency is the one free parameter of the point-to-point sweep: too few resident warps and a
+// level's rows are not all in flight; too many and far-ahead warps only add polling traffic.  The
+// tuner times the plan's own sweep for a few (block size, blocks per SM) candidates and keeps
+// the fastest; results are cached per matrix signature (rows, slab width, tail entries, levels,
+// value type, right-hand sides) so identical factors are tuned once per process.
+namespace {
+struct TuneKey {
+    int n, w, nlev, vdt, kp;
+    long long tail;
+    bool operator==(const TuneKey& o) const {
+        return n == o.n && w == o.w && nlev == o.nlev && vdt == o.vdt && kp == o.kp && tail == o.tail;
+    }
+};
+struct TuneKeyHash {
+    size_t operator()(const TuneKey& k) const {
+        return std::hash<long long>()(((long long)k.n * 1315423911LL) ^ (k.tail * 2654435761LL) ^ (k.nlev * 97) ^
+                                      (k.w * 31 + k.vdt * 7 + k.kp));
+    }
+};
+std::mutex g_tune_mu;
+std::unordered_map<TuneKey, std::pair<int, int>, TuneKeyHash> g_tune_cache;
+}  // namespace
+
+HEC_API hec_status sptrsv_autotune(sptrsv_plan* p, int nrhs, hec_tune* out, void* stream) {
+    clear_error();
+    if (!p || nrhs < 1 || nrhs > p->max_nrhs) return set_error(HEC_ERR_INVALID_ARG, "sptrsv_autotune: bad argument");
+    cudaStream_t s = S(stream);
+    const hec_matrix* T = p->T;
+    int kp = 1;
+    while (kp < nrhs) kp <<= 1;
+    TuneKey key{T->n, T->w, p->lv->nlev, (int)T->vdt, kp, T->tail_nnz};
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            p->threads = it->second.first;
+            p->blocks = it->second.second;
+            if (out) { *out = hec_tune{}; out->block_threads = p->threads; out->blocks_per_sm = p->blocks; }
+            return HEC_OK;
+        }
+    }
+    double* b = nullptr;
+    double* x = nullptr;
+    const size_t cnt = (size_t)std::max(T->n, 1) * nrhs;
+    HEC_CHECK(dalloc(&b, cnt));
+    hec_status st = dalloc(&x, cnt);
+    if (st) { cudaFree(b); return st; }
+    cudaMemsetAsync(b, 0, sizeof(double) * cnt, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int saved_t = p->threads, saved_b = p->blocks;
+    float best = 1e30f;
+    int bt = saved_t, bb = saved_b;
+    const int cand_t[2] = {128, 256};
+    const int cand_b[4] = {2, 4, 8, 16};
+    for (int ti = 0; ti < 2 && st == HEC_OK; ++ti) {
+        for (int bi = 0; bi < 4 && st == HEC_OK; ++bi) {
+            if (cand_t[ti] * cand_b[bi] > 2048) continue;
+            p->threads = cand_t[ti];
+            p->blocks = cand_b[bi];
+            st = sweep(p, nrhs, b, nrhs, p->lv->iperm, x, nrhs, p->lv->iperm, s);  // warm
+            if (st) break;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 3 && st == HEC_OK; ++r) st = sweep(p, nrhs, b, nrhs, p->lv->iperm, x, nrhs, p->lv->iperm, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (st == HEC_OK && ms < best) { best = ms; bt = cand_t[ti]; bb = cand_b[bi]; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(b);
+    cudaFree(x);
+    if (st) { p->threads = saved_t; p->blocks = saved_b; return st; }
+    p->threads = bt;
+    p->blocks = bb;
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune_cache[key] = {bt, bb};
+    }
+    if (out) { *out = hec_tune{}; out->block_threads = bt; out->blocks_per_sm = bb; }
+    return hec_sync_status(p, stream);
+}
+
 HEC_API hec_status hec_sync_status(const sptrsv_plan* p, void* stream) {
     if (!p) return set_error(HEC_ERR_INVALID_ARG, "hec_sync_status: NULL");
     int h = 0;

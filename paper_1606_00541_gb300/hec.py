@@ -315,6 +315,16 @@ def _solve(fn, name, plan, b, x, stream):
     return x
 
 
+_sptrsv_autotune = _sig("sptrsv_autotune", _vp, _i, ctypes.POINTER(HecTune), _vp)
+
+
+def sptrsv_autotune(plan, nrhs=1, stream=None):
+    """Times the plan's sweep over candidate launch shapes and keeps the fastest; returns it."""
+    t = HecTune()
+    _check(_sptrsv_autotune(plan.h, int(nrhs), ctypes.byref(t), _stream(stream)), "sptrsv_autotune")
+    return dict(block_threads=t.block_threads, blocks_per_sm=t.blocks_per_sm)
+
+
 def sptrsv_lower(plan, b, x=None, stream=None):
     return _solve(_sptrsv_lower, "sptrsv_lower", plan, b, x, stream)
 
@@ -375,6 +385,48 @@ def ilu_factor(rowptr, col, val, k=0, stream=None):
     return Csr(L.value), Csr(U.value)
 
 
+_ras_setup = _sig("ras_setup", _i, _vp, _vp, _vp, _vp, _i, ctypes.POINTER(_vp), _vp)
+_hec_ras_get = _sig("hec_ras_get", _vp, ctypes.POINTER(_i), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                    ctypes.POINTER(_vp), ctypes.POINTER(_vp))
+_hec_ras_destroy = _sig("hec_ras_destroy", _vp)
+
+
+class Ras(_Handle):
+    """RAS subdomain system built by ras_setup (Sec. 3, Eq. 4)."""
+    _destroy = staticmethod(_hec_ras_destroy)
+
+    def _get(self):
+        ne = _i()
+        p = [_vp() for _ in range(4)]
+        _check(_hec_ras_get(self.h, ctypes.byref(ne), *[ctypes.byref(x) for x in p]), "hec_ras_get")
+        return ne.value, [x.value for x in p]
+
+    @property
+    def n_ext(self):
+        return self._get()[0]
+
+    def tensors(self, nsub):
+        """(ext_ptr, ext2glob, owned (uint8), A_ext CSR tensors), device copies."""
+        ne, (ep, e2g, own, aext) = self._get()
+        n, nnz = _i(), _ll()
+        q = [_vp() for _ in range(3)]
+        _check(_hec_csr_get(aext, ctypes.byref(n), ctypes.byref(nnz), *[ctypes.byref(x) for x in q]), "hec_csr_get")
+        owned = torch.as_tensor(_DevArray(own, ne, "|u1", self), device="cuda").clone() if ne else \
+            torch.zeros(0, dtype=torch.uint8, device="cuda")
+        return (_view(ep, nsub + 1, torch.int32, self).clone(), _view(e2g, ne, torch.int32, self).clone(), owned,
+                (_view(q[0].value, n.value + 1, torch.int32, self).clone(),
+                 _view(q[1].value, nnz.value, torch.int32, self).clone(),
+                 _view(q[2].value, nnz.value, torch.float64, self).clone()))
+
+
+def ras_setup(rowptr, col, val, part, nsub, stream=None):
+    n = rowptr.numel() - 1
+    out = _vp()
+    _check(_ras_setup(n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(part), int(nsub), ctypes.byref(out),
+                      _stream(stream)), "ras_setup")
+    return Ras(out.value)
+
+
 # --- convenience: a full ILU solver assembled from the entry points ------------------------------
 
 class IluSolver:
@@ -391,8 +443,37 @@ class IluSolver:
         self.M = ilu_create(self.pL, self.pU)
         self.A = hec_from_csr(*A, vdt="f64", stream=stream) if A is not None else None
 
+    def autotune(self, nrhs=1, stream=None):
+        """Runs the sweep autotuner on both plans; returns the chosen launch shapes."""
+        return sptrsv_autotune(self.pL, nrhs, stream), sptrsv_autotune(self.pU, nrhs, stream)
+
     def apply(self, r, z=None, stream=None):
         return ilu_apply(self.M, r, z, stream)
 
     def solve(self, b, x=None, restart=30, rtol=1e-8, max_iters=1000, stream=None, **kw):
         return fgmres_solve(self.A, self.M, b, x, restart, rtol, max_iters, stream, **kw)
+
+
+class RasSolver(IluSolver):
+    """RAS preconditioner (Sec. 3, Eq. 4): ras_setup on the GPU, ILU(0) of the block-diagonal
+    subdomain system, one pair of batched sweeps for all subdomains, restricted write-back.
+    Pass `factors=(L, U)` to use given block-diagonal factors instead of the GPU ILU(0)."""
+
+    def __init__(self, A, part, nsub, vdt="f32", max_nrhs=1, stream=None, factors=None, **tune):
+        self.R = ras_setup(*A, part, nsub, stream)
+        self.ext_ptr, self.ext2glob, self.owned, self.A_ext = self.R.tensors(nsub)
+        if factors is None:
+            Lh, Uh = ilu_factor(*self.A_ext, k=0, stream=stream)
+            L, U = Lh.tensors(), Uh.tensors()
+        else:
+            L, U = factors
+        self.L, self.U = L, U
+        self.lvL = sptrsv_analyze(L[0], L[1], 0, stream)
+        self.lvU = sptrsv_analyze(U[0], U[1], 1, stream)
+        self.HL = hec_from_csr(*L, levels=self.lvL, vdt=vdt, stream=stream)
+        self.HU = hec_from_csr(*U, levels=self.lvU, vdt=vdt, stream=stream)
+        self.pL = sptrsv_plan_create(self.HL, self.lvL, max_nrhs, **tune)
+        self.pU = sptrsv_plan_create(self.HU, self.lvU, max_nrhs, **tune)
+        n = A[0].numel() - 1
+        self.M = ilu_create(self.pL, self.pU, n_glob=n, ext2glob=self.ext2glob, owned=self.owned)
+        self.A = hec_from_csr(*A, vdt="f64", stream=stream)
