@@ -125,6 +125,27 @@ struct hec_csr {
 };
 
 namespace hec {
+// Lane layout of the sweep: nrhs right-hand sides are padded to KP = the next power of two; one
+// right-hand side runs a lane per row, more run G per lane (4 for FP32 work, 2 for FP64) and
+// KP / G lanes per row.  The level-ordered solution has a row stride of KP values, and the chunk
+// table used is the one for 32 / lanes-per-row rows per warp.
+inline int sweep_kp(int nrhs) {
+    int kp = 1;
+    while (kp < nrhs) kp <<= 1;
+    return kp;
+}
+inline int sweep_lpr(int nrhs, hec_dtype vdt) {
+    if (nrhs <= 1) return 1;
+    const int kp = sweep_kp(nrhs);
+    const int g = vdt == HEC_F64 ? 2 : (kp >= 4 ? 4 : 2);
+    return kp / g;
+}
+inline int log2i(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
 // sweep launcher shared by sptrsv_* and ilu_apply: gather[r] is the row of b feeding new row r
 // (NULL = identity), scatter[r] the row of x receiving it (NULL = identity, -1 = skip).
 hec_status sweep(const sptrsv_plan* p, int nrhs, const double* b, int ldb, const int* gather, double* x,

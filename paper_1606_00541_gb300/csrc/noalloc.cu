@@ -137,17 +137,16 @@ HEC_API hec_status sptrsv_solve_noalloc(const hec_matrix* tri, const hec_levels*
     if (status_out) *status_out = 0;
     const int n = tri->n, nlev = lv->nlev;
     if (n == 0) return HEC_OK;
-    int kp = 1;
-    while (kp < nrhs) kp <<= 1;
-    const int kp_idx = kp == 1 ? 0 : kp == 2 ? 1 : kp == 4 ? 2 : kp == 8 ? 3 : 4;
-    const int rpw = 32 / kp;
+    const int kp = sweep_kp(nrhs);                        // padded row stride of the solution
+    const int kp_idx = log2i(sweep_lpr(nrhs, tri->vdt));  // lane layout -> chunk table
+    const int rpw = 32 >> kp_idx;
     // layout: [status | chunk prefix (nlev+1) | chunk table | level-ordered solution]
     const size_t chunk_cap = (size_t)nlev + ((size_t)n + rpw - 1) / rpw;
     const size_t off_cptr = 256;
     const size_t off_tbl = off_cptr + align256(sizeof(int) * ((size_t)nlev + 1));
     const size_t off_xp = off_tbl + align256(sizeof(int2) * chunk_cap);
     const size_t ws = tri->vdt == HEC_F64 ? 8 : 4;
-    const size_t xp_bytes = ws * (size_t)n * nrhs;
+    const size_t xp_bytes = ws * (size_t)n * kp;
     const size_t off_dinv = off_xp + align256(xp_bytes);
     const size_t need = off_dinv + align256(ws * (size_t)n);
     if (need > kScratchBytes)

@@ -250,6 +250,204 @@ __global__ void __launch_bounds__(256) k_sweep(SweepParams p) {
     }
 }
 
+// ---- several right-hand sides per lane ------------------------------------------------------
+// For nrhs > 1 a lane carries G consecutive right-hand sides of one row (G = 4 for FP32 work,
+// 2 for FP64) and moves them with one 16-byte (or 8-byte) relaxed vector access; LPR = KP / G
+// lanes serve a row, so a warp covers 32 / LPR rows of a level.  The level-ordered solution
+// is stored with a padded row stride of KP values; padded right-hand sides carry zeros.  Every
+// element is a single-copy-atomic word, so a consumer checks each one against the sentinel.
+template <typename XT, int G> struct VecIO;
+template <> struct VecIO<float, 2> {
+    __device__ static void load(const float* p, unsigned (&w)[2]) {
+        asm volatile("ld.relaxed.gpu.global.v2.b32 {%0, %1}, [%2];" : "=r"(w[0]), "=r"(w[1]) : "l"(p));
+    }
+    __device__ static void store(float* p, const unsigned (&w)[2]) {
+        asm volatile("st.relaxed.gpu.global.v2.b32 [%0], {%1, %2};" ::"l"(p), "r"(w[0]), "r"(w[1]) : "memory");
+    }
+};
+template <> struct VecIO<float, 4> {
+    __device__ static void load(const float* p, unsigned (&w)[4]) {
+        asm volatile("ld.relaxed.gpu.global.v4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "l"(p));
+    }
+    __device__ static void store(float* p, const unsigned (&w)[4]) {
+        asm volatile("st.relaxed.gpu.global.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(w[0]), "r"(w[1]),
+                     "r"(w[2]), "r"(w[3]) : "memory");
+    }
+};
+template <> struct VecIO<double, 2> {
+    __device__ static void load(const double* p, unsigned long long (&w)[2]) {
+        asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(w[0]), "=l"(w[1]) : "l"(p));
+    }
+    __device__ static void store(double* p, const unsigned long long (&w)[2]) {
+        asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(w[0]), "l"(w[1]) : "memory");
+    }
+};
+
+template <typename XT, typename AT, int NS, int G>
+struct DepBatchV {
+    typedef Word<XT> W;
+    typedef typename W::T WT;
+    const XT* addr[NS];
+    WT raw[NS][G];
+    AT v[NS];
+    unsigned valid, pend;
+    __device__ __forceinline__ void clear(const XT* base) {
+        valid = pend = 0;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            addr[k] = base;
+            v[k] = AT(0);
+#pragma unroll
+            for (int g = 0; g < G; ++g) raw[k][g] = 0;
+        }
+    }
+    __device__ __forceinline__ void set(int k, const XT* a, AT coef) {
+        addr[k] = a;
+        v[k] = coef;
+        valid |= 1u << k;
+        pend |= 1u << k;
+    }
+    __device__ __forceinline__ void poll() {
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            if (pend & (1u << k)) {
+                VecIO<XT, G>::load(addr[k], raw[k]);
+                bool ready = true;
+#pragma unroll
+                for (int g = 0; g < G; ++g) ready = ready && raw[k][g] != W::kSent;
+                if (ready) pend &= ~(1u << k);
+            }
+        }
+    }
+    __device__ __forceinline__ void wait(int* status, long long budget, int backoff_ns) {
+        if (!__any_sync(kFull, pend)) return;
+        const long long t0 = clock64();
+        for (unsigned it = 1;; ++it) {
+            if (backoff_ns) __nanosleep(backoff_ns);
+            poll();
+            if (!__any_sync(kFull, pend)) return;
+            if ((it & 31u) == 0u) {
+                bool give_up = (clock64() - t0 > budget) || (ld_relaxed_u32(status) != 0u);
+                if (__any_sync(kFull, give_up)) {
+                    record(status, HEC_ERR_TIMEOUT);
+#pragma unroll
+                    for (int k = 0; k < NS; ++k)
+#pragma unroll
+                        for (int g = 0; g < G; ++g)
+                            if (pend & (1u << k)) raw[k][g] = 0;
+                    return;
+                }
+            }
+        }
+    }
+    __device__ __forceinline__ void accumulate(AT (&acc)[G]) const {
+#pragma unroll
+        for (int k = 0; k < NS; ++k)
+            if (valid & (1u << k))
+#pragma unroll
+                for (int g = 0; g < G; ++g) acc[g] = fma(-v[k], (AT)W::val(raw[k][g]), acc[g]);
+    }
+};
+
+template <typename VT, typename XT, int LPR, int G, int WMAX>
+__global__ void __launch_bounds__(256) k_sweep_vec(SweepParams p) {
+    typedef typename Acc<XT>::T AT;
+    typedef Word<XT> W;
+    constexpr int KS = LPR * G;   // padded row stride of the level-ordered solution
+    constexpr int RPW = 32 / LPR;  // rows per warp step
+    const int lane = threadIdx.x & 31;
+    const int rsub = lane / LPR, q0 = (lane % LPR) * G;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const VT* __restrict__ ev = (const VT*)p.ell_val;
+    const VT* __restrict__ tv = (const VT*)p.tval;
+    XT* xp = (XT*)p.xp;
+    const int K = p.K;
+    (void)RPW;
+    for (int c = gw; c < p.nchunks; c += nw) {
+        const int2 ch = __ldg(p.chunks + c);
+        const int r = ch.x + rsub;
+        const bool act = rsub < ch.y;
+        AT acc[G];
+        AT diag = AT(1);
+        int t0 = 0, tl = 0, sr = -1;
+#pragma unroll
+        for (int g = 0; g < G; ++g) acc[g] = AT(0);
+        if (act) {
+            const int gr = p.gather ? __ldg(p.gather + r) : r;
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+                if (q0 + g < K) acc[g] = (AT)__ldg(p.b + (long)gr * p.ldb + q0 + g);
+            t0 = __ldg(p.tptr + r);
+            const int t1 = __ldg(p.tptr + r + 1) - 1;
+            tl = t1 - t0;
+            diag = p.dinv ? (AT)__ldg((const XT*)p.dinv + r) : ldv<VT, AT>(tv + t1);
+            sr = p.scatter ? __ldg(p.scatter + r) : r;
+        }
+        DepBatchV<XT, AT, WMAX, G> slab;
+        slab.clear(xp);
+#pragma unroll
+        for (int k = 0; k < WMAX; ++k) {
+            if (act && k < p.w) {
+                const long s = (long)k * p.ld + r;
+                const int cc = __ldg(p.ell_col + s);
+                if (cc >= 0) slab.set(k, xp + (long)cc * KS + q0, ldv<VT, AT>(ev + s));
+            }
+        }
+        slab.poll();
+        slab.wait(p.status, p.budget, p.backoff_ns);
+        slab.accumulate(acc);
+        for (int k = WMAX; k < p.w; ++k) {
+            DepBatchV<XT, AT, 1, G> one;
+            one.clear(xp);
+            if (act) {
+                const long s = (long)k * p.ld + r;
+                const int cc = __ldg(p.ell_col + s);
+                if (cc >= 0) one.set(0, xp + (long)cc * KS + q0, ldv<VT, AT>(ev + s));
+            }
+            one.poll();
+            one.wait(p.status, p.budget, p.backoff_ns);
+            one.accumulate(acc);
+        }
+        const int tmax = __reduce_max_sync(kFull, tl);
+        for (int tb = 0; tb < tmax; tb += kTailBatch) {
+            DepBatchV<XT, AT, kTailBatch, G> tail;
+            tail.clear(xp);
+#pragma unroll
+            for (int k = 0; k < kTailBatch; ++k) {
+                if (tb + k < tl) {
+                    const int cc = __ldg(p.tcol + t0 + tb + k);
+                    tail.set(k, xp + (long)cc * KS + q0, ldv<VT, AT>(tv + t0 + tb + k));
+                }
+            }
+            tail.poll();
+            tail.wait(p.status, p.budget, p.backoff_ns);
+            tail.accumulate(acc);
+        }
+        if (act) {
+            typename W::T outw[G];
+            AT xr[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                xr[g] = p.dinv ? acc[g] * diag : acc[g] / diag;
+                const XT xv = q0 + g < K ? (XT)xr[g] : XT(0);
+                typename W::T wv;
+                if (sizeof(XT) == 8) wv = (typename W::T)__double_as_longlong((double)xv);
+                else wv = (typename W::T)__float_as_uint((float)xv);
+                if (wv == W::kSent) wv = sizeof(XT) == 8 ? (typename W::T)0x7FF8000000000000ull : (typename W::T)0x7FC00000u;
+                outw[g] = wv;
+            }
+            // publish first (the next level waits on it), then the scatter to the caller's x
+            if (r != p.skip_row) VecIO<XT, G>::store(xp + (long)r * KS + q0, outw);
+            if (sr >= 0)
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (q0 + g < K) p.x[(long)sr * p.ldx + q0 + g] = (double)xr[g];
+        }
+    }
+}
+
 template <typename XT>
 __global__ void k_fill_sentinel(XT* xp, long count) {
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -303,13 +501,44 @@ hec_status launch_sweep(const sptrsv_plan* pl, SweepParams& sp, cudaStream_t s) 
     return HEC_OK;
 }
 
+template <typename VT, typename XT, int LPR, int G, int WMAX>
+hec_status launch_sweep_vec(const sptrsv_plan* pl, SweepParams& sp, cudaStream_t s) {
+    const void* k = (const void*)k_sweep_vec<VT, XT, LPR, G, WMAX>;
+    const int threads = pl->threads;
+    int per_sm = occupancy(k, threads);
+    if (per_sm <= 0) return set_error(HEC_ERR_CUDA, "sweep kernel cannot be resident");
+    if (pl->blocks > 0) per_sm = std::min(per_sm, pl->blocks);
+    constexpr int idx = LPR == 1 ? 0 : LPR == 2 ? 1 : LPR == 4 ? 2 : LPR == 8 ? 3 : 4;
+    if (!pl->chunks[idx]) return set_error(HEC_ERR_INVALID_ARG, "sweep: nrhs above the plan's max_nrhs");
+    sp.chunks = pl->chunks[idx];
+    sp.nchunks = pl->nchunks[idx];
+    const long want = ((long)sp.nchunks + threads / 32 - 1) / (threads / 32);
+    const int blocks = (int)std::max(1L, std::min((long)per_sm * num_sms(), want));
+    const long count = (long)sp.n * LPR * G;
+    const int fb = (int)std::min(4096L, std::max(1L, (count + 255) / 256));
+    {
+        ProfScope ps_(s, PROF_FILL);
+        k_fill_sentinel<XT><<<fb, 256, 0, s>>>((XT*)sp.xp, count);
+    }
+    HEC_LAUNCHED();
+    void* args[] = {&sp};
+    void* tok = nullptr;
+    profile_begin(s, &tok);
+    HEC_CUDA(cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(threads), args, 0, s));
+    profile_end(s, tok);
+    count_launch();
+    return HEC_OK;
+}
+
+// one right-hand side: lane per row; more: G right-hand sides per lane, LPR lanes per row
 template <typename VT, typename XT, int WMAX>
 hec_status dispatch_k(const sptrsv_plan* pl, SweepParams& sp, cudaStream_t s) {
+    constexpr int G = sizeof(XT) == 8 ? 2 : 4;
     if (sp.K <= 1) return launch_sweep<VT, XT, 1, WMAX>(pl, sp, s);
-    if (sp.K <= 2) return launch_sweep<VT, XT, 2, WMAX>(pl, sp, s);
-    if (sp.K <= 4) return launch_sweep<VT, XT, 4, WMAX>(pl, sp, s);
-    if (sp.K <= 8) return launch_sweep<VT, XT, 8, WMAX>(pl, sp, s);
-    return launch_sweep<VT, XT, 16, WMAX>(pl, sp, s);
+    if (sp.K <= 2) return launch_sweep_vec<VT, XT, 1, 2, WMAX>(pl, sp, s);
+    if (sp.K <= 4) return launch_sweep_vec<VT, XT, 4 / G, G, WMAX>(pl, sp, s);
+    if (sp.K <= 8) return launch_sweep_vec<VT, XT, 8 / G, G, WMAX>(pl, sp, s);
+    return launch_sweep_vec<VT, XT, 16 / G, G, WMAX>(pl, sp, s);
 }
 
 // slab slots held in registers: 4 covers the 5- and 7-point ILU(0) factors, 8 the wider ones
@@ -368,9 +597,11 @@ hec_status build_chunks(sptrsv_plan* p) {
     HEC_CHECK(dalloc(&cptr, (size_t)nlev + 1));
     hec_status st = HEC_OK;
     cudaStream_t s = 0;
+    unsigned needed = 0;  // only the lane layouts this plan can be called with
+    for (int k = 1; k <= p->max_nrhs; ++k) needed |= 1u << log2i(sweep_lpr(k, p->T->vdt));
     for (int i = 0; i < 5 && st == HEC_OK; ++i) {
-        const int kp = 1 << i, rpw = 32 / kp;
-        if (i > 0 && (kp >> 1) >= p->max_nrhs) break;  // only the widths this plan can be called with
+        const int rpw = 32 >> i;
+        if (!(needed & (1u << i))) continue;
         if (nlev > 0) {
             k_chunk_counts<<<(nlev + 255) / 256, 256, 0, s>>>(nlev, lv->level_ptr, rpw, cptr);
             count_launch();
@@ -479,7 +710,7 @@ HEC_API hec_status sptrsv_plan_create(const hec_matrix* tri, const hec_levels* l
         delete p;
         return set_error(HEC_ERR_INVALID_ARG, "sptrsv_plan_create: block_threads must be a multiple of 32 in [32, 256]");
     }
-    hec_status st = dmalloc(&p->xp, work_size(tri->vdt) * (size_t)tri->n * max_nrhs + 16);
+    hec_status st = dmalloc(&p->xp, work_size(tri->vdt) * (size_t)tri->n * sweep_kp(max_nrhs) + 16);
     if (st == HEC_OK) st = dalloc(&p->status, 1);
     if (st == HEC_OK && cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) st = cuda_error(cudaGetLastError(), "memset");
     if (st == HEC_OK) st = build_chunks(p);
