@@ -140,10 +140,12 @@ def round_f32_bits(d):
 
 
 def round_bf16_bits(d):
-    f = lib().or_round_bf16_bits
-    f.restype = ctypes.c_uint32
-    f.argtypes = [ctypes.c_double]
-    return np.array([f(float(x)) for x in np.ravel(d)], dtype=np.uint16)
+    a = np.ascontiguousarray(np.ravel(d), dtype=np.float64)
+    out = np.zeros(max(len(a), 1), dtype=np.uint16)
+    f = lib().or_round_bf16_array
+    f.restype = None
+    f(ctypes.c_long(len(a)), _p(a), _p(out))
+    return out[:len(a)]
 
 
 # --- HEC (Sec. 2.1, Alg. 1) -----------------------------------------------------------------

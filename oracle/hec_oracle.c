@@ -202,6 +202,12 @@ OR_EXPORT uint32_t or_round_bf16_bits(double d)
     return sign | ((u >> 16) & 0x7FFFu);
 }
 
+/* Array form of or_round_bf16_bits. */
+OR_EXPORT void or_round_bf16_array(long n, const double* in, uint16_t* out)
+{
+    for (long i = 0; i < n; ++i) out[i] = (uint16_t)or_round_bf16_bits(in[i]);
+}
+
 static double bf16_bits_to_double(uint32_t h)
 {
     uint32_t u = (h & 0xFFFFu) << 16;
