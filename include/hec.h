@@ -244,9 +244,65 @@ typedef struct {
  * once per inner iteration (the Hessenberg column is solved on the host).  Returns
  * HEC_ERR_NOT_CONVERGED when max_iters is reached, HEC_ERR_TIMEOUT when a sweep's dependency
  * wait timed out. */
-hec_status fgmres_solve(const hec_matrix* A, const ilu_precond* M, int nrhs, const double* b,
-                        int ldb, double* x, int ldx, int restart, double rtol, int max_iters,
-                        hec_fgmres_info* info /* host */, void* stream);
+typedef struct hec_stage hec_stage;
+hec_status fgmres_solve(const hec_matrix* A, const ilu_precond* M, const hec_stage* extra,
+                        int nrhs, const double* b, int ldb, double* x, int ldx, int restart,
+                        double rtol, int max_iters, hec_fgmres_info* info /* host */,
+                        void* stream);
+/* `extra` (may be NULL) is a learned correction stage (stage_create below) applied after M in
+ * every iteration; it requires M and nrhs = 1. */
+
+/* ---------------------------------------------------------------------------------------- */
+/* Learned correction stage (not in the paper): a 4-layer 3x3x3 convolutional network, 2 -> 16 */
+/* -> 16 -> 16 -> 1 channels, ReLU between layers, BF16 weights and activations with FP32      */
+/* accumulation on the tensor cores, trained on (residual, error) pairs of the FP64 solver      */
+/* ---------------------------------------------------------------------------------------- */
+
+typedef struct hec_net hec_net;
+
+/* Number of FP32 parameters: 4 layers x (27 taps x 16 in x 16 out weights + 16 biases).  Layer l
+ * occupies [l * 6928, (l+1) * 6928): weight (tap, ci, co) at (tap*16 + ci)*16 + co with
+ * tap = (dz*3 + dy)*3 + dx (offsets dz-1, dy-1, dx-1), then the 16 biases.  Channels the network
+ * does not use (inputs 2..15 of layer 0, outputs 1..15 of layer 3) should be zero. */
+int net_param_count(void);
+/* params: host FP32 array of net_param_count() values (the initialization). */
+hec_status net_create(const float* params, hec_net** out);
+hec_status net_destroy(hec_net* net);
+/* Host copies of the FP32 parameters and of the last computed gradients (either may be NULL). */
+hec_status net_get_params(const hec_net* net, float* params, float* grads);
+hec_status net_set_params(hec_net* net, const float* params);
+/* Forward pass on a field of nx*ny*nz voxels (x fastest) made of nz/zs samples of zs planes
+ * stacked along z (each sample padded with zeros at its own boundary).  x_in: device BF16,
+ * channels-last, 16 channels per voxel (channels 0 and 1 used).  acts_out (may be NULL): device
+ * BF16 [4][nvox][16], the outputs of the four layers (after ReLU for the first three).  out (may
+ * be NULL): device FP32 [nvox], channel 0 of the last layer before rounding to BF16. */
+hec_status net_forward(hec_net* net, int nx, int ny, int nz, int zs, const void* x_in,
+                       void* acts_out, float* out, void* stream);
+/* One training step on a minibatch laid out as in net_forward: forward, mean-squared error
+ * against target (device FP32 [nvox]), backward (gradients kept, see net_get_params) and, when
+ * update != 0, one Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected) with rate lr.
+ * loss_out (host, may be NULL) receives the loss and then the call synchronizes `stream`. */
+hec_status net_train_step(hec_net* net, int nx, int ny, int nz, int zs, const void* x_in,
+                          const float* target, float lr, int update, float* loss_out,
+                          void* stream);
+
+/* A training sample from one residual / error pair on an n-voxel field: sigma = RMS(r) (device
+ * FP64, *sigma_out), x_out = channels-last BF16 [n][16] with channel 0 = r / sigma, channel 1 =
+ * aux_scale * aux, the rest 0, and target_out (may be NULL) = e / sigma in FP32 [n]. */
+hec_status net_make_sample(int n, const double* r, const double* e, const double* aux,
+                           double aux_scale, void* x_out, float* target_out, double* sigma_out,
+                           void* stream);
+
+/* The stage used by fgmres_solve: with z1 = M^-1 v (the ILU sweep) and r1 = v - A z1,
+ * c = sigma * Net([r1 / sigma, aux_scale * aux]) with sigma = RMS(r1), alpha = <r1, A c> /
+ * <A c, A c>, and z = z1 + alpha c when alpha > 0 and ||r1 - alpha A c|| < rho ||r1||, else z = z1
+ * (the plain ILU result: the fallback).  A: the FP64 general-mode matrix on an nx*ny*nz grid;
+ * aux: device FP64 [n] second input field (e.g. ln k), copied.  The net is borrowed. */
+hec_status stage_create(hec_net* net, const hec_matrix* A, int nx, int ny, int nz,
+                        const double* aux, double aux_scale, double rho, hec_stage** out);
+/* Applications and accepted corrections since creation or the last reset. */
+hec_status stage_stats(const hec_stage* stage, int* applied, int* accepted, int reset);
+hec_status stage_destroy(hec_stage* stage);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Incomplete factorizations on the GPU (Sec. 3): ILU(0) and ILU(1) of a CSR matrix            */

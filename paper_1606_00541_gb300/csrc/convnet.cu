@@ -1,0 +1,574 @@
+// The learned correction network: four 3x3x3 'same' convolutions (2 -> 16 -> 16 -> 16 -> 1
+// channels, ReLU between layers), BF16 weights and activations with FP32 accumulation on the
+// tensor cores, and its training (backward pass, MSE loss, Adam).  Not part of the paper: it is
+// a flexible-preconditioner stage applied after the ILU sweep.
+//
+// Layout: a field on an nx x ny x nz grid (x fastest) is stored channels-last with 16 BF16
+// channels per voxel (32 bytes); unused channels are zero.  Several samples may be stacked along
+// z (zs planes each); the convolution treats the sample boundaries as zero padding.
+//
+// Convolution = implicit GEMM: for each of the 27 taps, D[voxels x 16 out] += X_shifted[voxels x
+// 16 in] * W_tap[16 in x 16 out], one mma.sync.m16n8k16 (BF16 in, FP32 accumulate) per 16
+// voxels per 8 output channels per tap.  A block computes a 32 x 4 x 1 voxel tile from a 34 x 6 x 3
+// halo tile staged in shared memory together with all 27 weight taps.  The data gradient is the
+// same kernel run with the spatially flipped, channel-transposed weights and the ReLU mask of
+// the layer applied while the halo is staged; the weight gradient is a GEMM over voxels with
+// per-block partial sums reduced in a fixed order (deterministic).
+#include <cuda_bf16.h>
+
+#include <vector>
+
+#include "internal.cuh"
+
+namespace hec {
+namespace {
+
+constexpr int C = 16;                 // stored channels
+constexpr int TX = 32, TY = 4;         // output tile
+constexpr int HX = TX + 2, HY = TY + 2, HZ = 3;
+constexpr int NTAP = 27;
+constexpr int WSZ = NTAP * C * C;      // weights of one layer
+constexpr int PSZ = WSZ + C;           // + bias
+constexpr int NL = 4;                  // layers
+constexpr int kConvThreads = 128;      // 4 warps, one output row (y) each
+
+struct Geom {
+    int nx, ny, nz, zs;  // grid; samples of zs planes stacked along z
+};
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ unsigned pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+}
+
+// zero the channels whose mask value is not positive (ReLU derivative)
+__device__ __forceinline__ uint4 apply_mask(uint4 v, uint4 m) {
+    unsigned* pv = (unsigned*)&v;
+    const unsigned* pm = (const unsigned*)&m;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float m0 = __uint_as_float(pm[i] << 16), m1 = __uint_as_float(pm[i] & 0xFFFF0000u);
+        unsigned keep = (m0 > 0.f ? 0x0000FFFFu : 0u) | (m1 > 0.f ? 0xFFFF0000u : 0u);
+        pv[i] &= keep;
+    }
+    return v;
+}
+
+// Stage the 34 x 6 x 3 halo of tile (bx, by, bz) into shared memory (zero outside the grid or the
+// sample), masked by `mask` when given.
+__device__ __forceinline__ void load_halo(const Geom& g, const __nv_bfloat16* __restrict__ X,
+                                          const __nv_bfloat16* __restrict__ mask, int bx, int by, int bz,
+                                          __nv_bfloat16 (*sx)[HY][HX][C]) {
+    const int sample = bz / g.zs, zl = bz - sample * g.zs;
+    for (int i = threadIdx.x; i < HZ * HY * HX * 2; i += blockDim.x) {
+        const int v = i >> 1, half = i & 1;
+        const int hx = v % HX, hy = (v / HX) % HY, hz = v / (HX * HY);
+        const int x = bx + hx - 1, y = by + hy - 1, z = zl + hz - 1;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.zs) {
+            const long gi = (((long)sample * g.zs + z) * g.ny + y) * g.nx + x;
+            val = __ldg((const uint4*)X + gi * 2 + half);
+            if (mask) val = apply_mask(val, __ldg((const uint4*)mask + gi * 2 + half));
+        }
+        ((uint4*)&sx[0][0][0][0])[v * 2 + half] = val;
+    }
+}
+
+// Y = conv(X, W) + bias, optional ReLU; Y0 (optional) receives channel 0 in FP32 times y0_scale.
+// W is [27][16 out][16 in] BF16.
+__global__ void __launch_bounds__(kConvThreads) k_conv_fwd(Geom g, const __nv_bfloat16* __restrict__ X,
+                                                           const __nv_bfloat16* __restrict__ mask,
+                                                           const __nv_bfloat16* __restrict__ W,
+                                                           const float* __restrict__ bias, int relu,
+                                                           __nv_bfloat16* __restrict__ Y, float* __restrict__ Y0,
+                                                           float y0_scale) {
+    __shared__ __align__(16) __nv_bfloat16 sx[HZ][HY][HX][C];
+    __shared__ __align__(16) __nv_bfloat16 sw[NTAP][C][C];
+    const int bx = blockIdx.x * TX, by = blockIdx.y * TY, bz = blockIdx.z;
+    for (int i = threadIdx.x; i < WSZ / 8; i += blockDim.x) ((uint4*)&sw[0][0][0])[i] = __ldg((const uint4*)W + i);
+    load_halo(g, X, mask, bx, by, bz, sx);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gq = lane >> 2, t = lane & 3;
+    float acc[2][2][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+#pragma unroll 3
+    for (int tap = 0; tap < NTAP; ++tap) {
+        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+        unsigned bf[2][2];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            bf[nt][0] = *(const unsigned*)&sw[tap][nt * 8 + gq][2 * t];
+            bf[nt][1] = *(const unsigned*)&sw[tap][nt * 8 + gq][2 * t + 8];
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const int hx = mt * 16 + gq + dx;
+            unsigned af[4];
+            af[0] = *(const unsigned*)&sx[dz][w + dy][hx][2 * t];
+            af[1] = *(const unsigned*)&sx[dz][w + dy][hx + 8][2 * t];
+            af[2] = *(const unsigned*)&sx[dz][w + dy][hx][2 * t + 8];
+            af[3] = *(const unsigned*)&sx[dz][w + dy][hx + 8][2 * t + 8];
+            mma_bf16(acc[mt][0], af, bf[0]);
+            mma_bf16(acc[mt][1], af, bf[1]);
+        }
+    }
+    const int y = by + w;
+    if (y >= g.ny) return;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int x = bx + mt * 16 + gq + half * 8;
+            if (x >= g.nx) continue;
+            const long vox = ((long)bz * g.ny + y) * g.nx + x;
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                const int co = nt * 8 + 2 * t;
+                float v0 = acc[mt][nt][half * 2 + 0], v1 = acc[mt][nt][half * 2 + 1];
+                if (bias) {
+                    v0 += bias[co];
+                    v1 += bias[co + 1];
+                }
+                if (relu) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                *(unsigned*)&Y[vox * C + co] = pack2(__float2bfloat16_rn(v0), __float2bfloat16_rn(v1));
+                if (Y0 && co == 0) Y0[vox] = v0 * y0_scale;
+            }
+        }
+    }
+}
+
+// Weight and bias gradients of one layer: partial[block][tap][ci][co] = sum over this tile's voxels
+// of Ain[v + off(tap)][ci] * dZ[v][co], partial[block][WSZ + co] = sum of dZ[v][co];
+// dZ = dA masked by the layer's ReLU (mask = its output) when mask is given.
+__global__ void __launch_bounds__(kConvThreads) k_conv_wgrad(Geom g, const __nv_bfloat16* __restrict__ Ain,
+                                                             const __nv_bfloat16* __restrict__ dA,
+                                                             const __nv_bfloat16* __restrict__ mask,
+                                                             float* __restrict__ partial) {
+    __shared__ __align__(16) __nv_bfloat16 sx[HZ][HY][HX][C];
+    __shared__ __align__(16) __nv_bfloat16 sd[TY][TX][C];
+    __shared__ float sbias[kConvThreads / 32][C];
+    const int bx = blockIdx.x * TX, by = blockIdx.y * TY, bz = blockIdx.z;
+    load_halo(g, Ain, nullptr, bx, by, bz, sx);
+    for (int i = threadIdx.x; i < TY * TX * 2; i += blockDim.x) {
+        const int v = i >> 1, half = i & 1;
+        const int lx = v % TX, ly = v / TX;
+        const int x = bx + lx, y = by + ly;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (x < g.nx && y < g.ny) {
+            const long gi = ((long)bz * g.ny + y) * g.nx + x;
+            val = __ldg((const uint4*)dA + gi * 2 + half);
+            if (mask) val = apply_mask(val, __ldg((const uint4*)mask + gi * 2 + half));
+        }
+        ((uint4*)&sd[0][0][0])[v * 2 + half] = val;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gq = lane >> 2, t = lane & 3;
+    const long pbase = (long)((blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * PSZ;
+    // taps w, w + 4, w + 8, ... for this warp
+    for (int tap = w; tap < NTAP; tap += 4) {
+        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+        float acc[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[nt][c] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < TX * TY / 16; ++ks) {
+            const int vy = (ks * 16) / TX, vx0 = (ks * 16) % TX;
+            // A[m = ci][k = voxel]: Ain at the shifted voxel
+            const __nv_bfloat16* srow = &sx[dz][vy + dy][0][0];
+            unsigned af[4];
+            af[0] = pack2(srow[(vx0 + 2 * t + dx) * C + gq], srow[(vx0 + 2 * t + 1 + dx) * C + gq]);
+            af[1] = pack2(srow[(vx0 + 2 * t + dx) * C + gq + 8], srow[(vx0 + 2 * t + 1 + dx) * C + gq + 8]);
+            af[2] = pack2(srow[(vx0 + 2 * t + 8 + dx) * C + gq], srow[(vx0 + 2 * t + 9 + dx) * C + gq]);
+            af[3] = pack2(srow[(vx0 + 2 * t + 8 + dx) * C + gq + 8], srow[(vx0 + 2 * t + 9 + dx) * C + gq + 8]);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                const int co = nt * 8 + gq;
+                unsigned bfr[2];
+                bfr[0] = pack2(sd[vy][vx0 + 2 * t][co], sd[vy][vx0 + 2 * t + 1][co]);
+                bfr[1] = pack2(sd[vy][vx0 + 2 * t + 8][co], sd[vy][vx0 + 2 * t + 9][co]);
+                mma_bf16(acc[nt], af, bfr);
+            }
+        }
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const int co = nt * 8 + 2 * t;
+            partial[pbase + (long)tap * C * C + gq * C + co] = acc[nt][0];
+            partial[pbase + (long)tap * C * C + gq * C + co + 1] = acc[nt][1];
+            partial[pbase + (long)tap * C * C + (gq + 8) * C + co] = acc[nt][2];
+            partial[pbase + (long)tap * C * C + (gq + 8) * C + co + 1] = acc[nt][3];
+        }
+    }
+    // bias gradient: warp w sums rows y = w of the tile
+    if (lane < C) {
+        float s = 0.f;
+        for (int x = 0; x < TX; ++x) s += __bfloat162float(sd[w][x][lane]);
+        sbias[w][lane] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float s = 0.f;
+        for (int i = 0; i < kConvThreads / 32; ++i) s += sbias[i][threadIdx.x];
+        partial[pbase + WSZ + threadIdx.x] = s;
+    }
+}
+
+// grad[j] = sum over blocks of partial[b][j], in block order
+__global__ void k_reduce_partials(int nblk, const float* __restrict__ partial, float* __restrict__ grad) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= PSZ) return;
+    float s = 0.f;
+    for (int b = 0; b < nblk; ++b) s += partial[(long)b * PSZ + j];
+    grad[j] = s;
+}
+
+// From FP32 master parameters P[tap][ci][co] (+ bias) to the BF16 forward layout Wf[tap][co][ci]
+// and the data-gradient layout Wd[26 - tap][ci][co] (flipped taps, channels transposed).
+__global__ void k_weights(const float* __restrict__ P, __nv_bfloat16* __restrict__ Wf, __nv_bfloat16* __restrict__ Wd) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= WSZ) return;
+    const int tap = j / (C * C), ci = (j / C) % C, co = j % C;
+    const __nv_bfloat16 v = __float2bfloat16_rn(P[j]);
+    Wf[(tap * C + co) * C + ci] = v;
+    Wd[((NTAP - 1 - tap) * C + ci) * C + co] = v;
+}
+
+__global__ void k_adam(int n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const float gj = g[j];
+    const float mj = b1 * m[j] + (1.f - b1) * gj;
+    const float vj = b2 * v[j] + (1.f - b2) * gj * gj;
+    m[j] = mj;
+    v[j] = vj;
+    p[j] -= lr * (mj / c1) / (sqrtf(vj / c2) + eps);
+}
+
+// dOut (16-channel BF16, channel 0 only) = 2 (out - target) / N; partial squared errors per block
+__global__ void k_mse(long nvox, const float* __restrict__ out, const float* __restrict__ target, float inv_n,
+                      __nv_bfloat16* __restrict__ dout, float* __restrict__ part) {
+    __shared__ float red[8];
+    float s = 0.f;
+    for (long v = (long)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (long)gridDim.x * blockDim.x) {
+        const float d = out[v] - target[v];
+        s += d * d;
+        uint4 z0 = make_uint4(0, 0, 0, 0), z1 = z0;
+        z0.x = (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(2.f * d * inv_n));
+        ((uint4*)dout)[v * 2] = z0;
+        ((uint4*)dout)[v * 2 + 1] = z1;
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        part[blockIdx.x] = t;
+    }
+}
+
+}  // namespace
+}  // namespace hec
+
+// ---- the network handle ----------------------------------------------------------------------
+struct hec_net {
+    float* P = nullptr;                // [NL][PSZ] FP32 master parameters
+    float* G = nullptr;                // gradients
+    float* M = nullptr;                // Adam first moment
+    float* V = nullptr;                // Adam second moment
+    __nv_bfloat16* Wf = nullptr;       // [NL][WSZ] forward weights
+    __nv_bfloat16* Wd = nullptr;       // [NL][WSZ] data-gradient weights
+    int step = 0;
+    long cap = 0;                      // voxels the activation buffers hold
+    __nv_bfloat16* act[hec::NL + 1] = {};  // act[0] = input, act[l] = output of layer l
+    __nv_bfloat16* dA[2] = {};
+    float* out = nullptr;              // FP32 channel 0 of the last layer
+    float* partial = nullptr;
+    long partial_cap = 0;
+    float* lpart = nullptr;
+};
+
+namespace hec {
+namespace {
+
+void free_net(hec_net* N) {
+    if (!N) return;
+    cudaFree(N->P); cudaFree(N->G); cudaFree(N->M); cudaFree(N->V); cudaFree(N->Wf); cudaFree(N->Wd);
+    for (auto& a : N->act) cudaFree(a);
+    for (auto& a : N->dA) cudaFree(a);
+    cudaFree(N->out); cudaFree(N->partial); cudaFree(N->lpart);
+    delete N;
+}
+
+hec_status ensure(hec_net* N, long nvox, long nblk) {
+    if (nvox > N->cap) {
+        for (auto& a : N->act) { cudaFree(a); a = nullptr; }
+        for (auto& a : N->dA) { cudaFree(a); a = nullptr; }
+        cudaFree(N->out);
+        N->out = nullptr;
+        N->cap = 0;
+        for (auto& a : N->act) HEC_CHECK(dalloc(&a, (size_t)nvox * C));
+        for (auto& a : N->dA) HEC_CHECK(dalloc(&a, (size_t)nvox * C));
+        HEC_CHECK(dalloc(&N->out, (size_t)nvox));
+        N->cap = nvox;
+    }
+    if (nblk > N->partial_cap) {
+        cudaFree(N->partial);
+        N->partial = nullptr;
+        HEC_CHECK(dalloc(&N->partial, (size_t)nblk * PSZ));
+        N->partial_cap = nblk;
+    }
+    return HEC_OK;
+}
+
+hec_status refresh_weights(hec_net* N, cudaStream_t s) {
+    for (int l = 0; l < NL; ++l)
+        k_weights<<<(WSZ + 255) / 256, 256, 0, s>>>(N->P + (long)l * PSZ, N->Wf + (long)l * WSZ, N->Wd + (long)l * WSZ);
+    count_launch(NL);
+    HEC_CUDA(cudaGetLastError());
+    return HEC_OK;
+}
+
+dim3 conv_grid(const Geom& g) { return dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, g.nz); }
+
+hec_status check_geom(const Geom& g) {
+    if (g.nx <= 0 || g.ny <= 0 || g.nz <= 0 || g.zs <= 0 || g.nz % g.zs != 0 || (g.ny + TY - 1) / TY > 65535 ||
+        g.nz > 65535)
+        return set_error(HEC_ERR_INVALID_ARG, "net: bad grid (need nz a multiple of zs, ny/4 and nz <= 65535)");
+    return HEC_OK;
+}
+
+// forward through all layers from N->act[0]; the FP32 output (times scale) lands in N->out
+hec_status forward(hec_net* N, const Geom& g, float scale, cudaStream_t s) {
+    const dim3 grid = conv_grid(g);
+    for (int l = 0; l < NL; ++l) {
+        const bool last = l == NL - 1;
+        ProfScope ps_(s, PROF_VEC);
+        k_conv_fwd<<<grid, kConvThreads, 0, s>>>(g, N->act[l], nullptr, N->Wf + (long)l * WSZ, N->P + (long)l * PSZ + WSZ,
+                                                 last ? 0 : 1, N->act[l + 1], last ? N->out : nullptr, scale);
+    }
+    count_launch(NL);
+    HEC_CUDA(cudaGetLastError());
+    return HEC_OK;
+}
+
+// backward from dA[0] = dLoss/dOutput (16-channel, channel 0); gradients into N->G
+hec_status backward(hec_net* N, const Geom& g, cudaStream_t s) {
+    const dim3 grid = conv_grid(g);
+    const long nblk = (long)grid.x * grid.y * grid.z;
+    int cur = 0;
+    for (int l = NL - 1; l >= 0; --l) {
+        const __nv_bfloat16* mask = l == NL - 1 ? nullptr : N->act[l + 1];  // ReLU of layer l
+        k_conv_wgrad<<<grid, kConvThreads, 0, s>>>(g, N->act[l], N->dA[cur], mask, N->partial);
+        k_reduce_partials<<<(PSZ + 255) / 256, 256, 0, s>>>((int)nblk, N->partial, N->G + (long)l * PSZ);
+        count_launch(2);
+        if (l > 0) {
+            k_conv_fwd<<<grid, kConvThreads, 0, s>>>(g, N->dA[cur], mask, N->Wd + (long)l * WSZ, nullptr, 0,
+                                                     N->dA[cur ^ 1], nullptr, 1.f);
+            count_launch();
+            cur ^= 1;
+        }
+    }
+    HEC_CUDA(cudaGetLastError());
+    return HEC_OK;
+}
+
+__global__ void k_pack_input(long nvox, const double* __restrict__ r, const double* __restrict__ sigma,
+                             const __nv_bfloat16* __restrict__ aux, __nv_bfloat16* __restrict__ X) {
+    const double inv = *sigma > 0.0 ? 1.0 / *sigma : 0.0;
+    for (long v = (long)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (long)gridDim.x * blockDim.x) {
+        uint4 z0 = make_uint4(0, 0, 0, 0), z1 = z0;
+        z0.x = pack2(__float2bfloat16_rn((float)(r[v] * inv)), aux[v]);
+        ((uint4*)X)[v * 2] = z0;
+        ((uint4*)X)[v * 2 + 1] = z1;
+    }
+}
+
+}  // namespace
+
+// used by the learned FGMRES stage (krylov.cu)
+hec_status net_apply_field(hec_net* N, int nx, int ny, int nz, const double* r, const double* sigma,
+                           const __nv_bfloat16* aux, cudaStream_t s) {
+    Geom g{nx, ny, nz, nz};
+    HEC_CHECK(check_geom(g));
+    const long nvox = (long)nx * ny * nz;
+    const dim3 grid = conv_grid(g);
+    HEC_CHECK(ensure(N, nvox, (long)grid.x * grid.y * grid.z));
+    {
+        ProfScope ps_(s, PROF_VEC);
+        k_pack_input<<<(int)std::min<long>((nvox + 255) / 256, 65536), 256, 0, s>>>(nvox, r, sigma, aux, N->act[0]);
+    }
+    count_launch();
+    return forward(N, g, 1.f, s);
+}
+const float* net_output(const hec_net* N) { return N->out; }
+
+}  // namespace hec
+
+using namespace hec;
+
+namespace hec {
+namespace {
+// one block: sum of squares of r[0..n) into out[0] (FP64)
+__global__ void k_sumsq(long n, const double* __restrict__ r, double* out) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (long i = threadIdx.x; i < n; i += blockDim.x) s = fma(r[i], r[i], s);
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        out[0] = sqrt(t / (double)n);  // sigma = RMS
+    }
+}
+__global__ void k_make_sample(long n, const double* __restrict__ r, const double* __restrict__ e,
+                              const double* __restrict__ aux, double aux_scale, const double* __restrict__ sigma,
+                              __nv_bfloat16* __restrict__ X, float* __restrict__ T) {
+    const double inv = *sigma > 0.0 ? 1.0 / *sigma : 0.0;
+    for (long v = (long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long)gridDim.x * blockDim.x) {
+        uint4 z0 = make_uint4(0, 0, 0, 0), z1 = z0;
+        z0.x = pack2(__float2bfloat16_rn((float)(r[v] * inv)), __float2bfloat16_rn((float)(aux[v] * aux_scale)));
+        ((uint4*)X)[v * 2] = z0;
+        ((uint4*)X)[v * 2 + 1] = z1;
+        if (T) T[v] = (float)(e[v] * inv);
+    }
+}
+}  // namespace
+}  // namespace hec
+
+HEC_API int net_param_count(void) { return NL * PSZ; }
+
+HEC_API hec_status net_make_sample(int n, const double* r, const double* e, const double* aux, double aux_scale,
+                                   void* x_out, float* target_out, double* sigma_out, void* stream) {
+    clear_error();
+    if (n <= 0 || !r || !aux || !x_out || !sigma_out || (target_out && !e))
+        return set_error(HEC_ERR_INVALID_ARG, "net_make_sample: bad argument");
+    cudaStream_t s = S(stream);
+    k_sumsq<<<1, 1024, 0, s>>>(n, r, sigma_out);
+    k_make_sample<<<(int)std::min<long>(((long)n + 255) / 256, 65536), 256, 0, s>>>(
+        n, r, e, aux, aux_scale, sigma_out, (__nv_bfloat16*)x_out, target_out);
+    count_launch(2);
+    HEC_CUDA(cudaGetLastError());
+    return HEC_OK;
+}
+
+HEC_API hec_status net_create(const float* params, hec_net** out) {
+    clear_error();
+    if (!params || !out) return set_error(HEC_ERR_INVALID_ARG, "net_create: NULL");
+    *out = nullptr;
+    hec_net* N = new hec_net();
+    const size_t np = (size_t)NL * PSZ;
+    hec_status st = HEC_OK;
+    if ((st = dalloc(&N->P, np)) || (st = dalloc(&N->G, np)) || (st = dalloc(&N->M, np)) || (st = dalloc(&N->V, np)) ||
+        (st = dalloc(&N->Wf, (size_t)NL * WSZ)) || (st = dalloc(&N->Wd, (size_t)NL * WSZ)) || (st = dalloc(&N->lpart, 4096))) {
+        free_net(N);
+        return st;
+    }
+    cudaMemcpy(N->P, params, sizeof(float) * np, cudaMemcpyHostToDevice);
+    cudaMemset(N->M, 0, sizeof(float) * np);
+    cudaMemset(N->V, 0, sizeof(float) * np);
+    cudaMemset(N->G, 0, sizeof(float) * np);
+    st = refresh_weights(N, 0);
+    if (st == HEC_OK && cudaDeviceSynchronize() != cudaSuccess) st = cuda_error(cudaGetLastError(), "net_create");
+    if (st) { free_net(N); return st; }
+    *out = N;
+    return HEC_OK;
+}
+
+HEC_API hec_status net_destroy(hec_net* N) {
+    free_net(N);
+    return HEC_OK;
+}
+
+HEC_API hec_status net_get_params(const hec_net* N, float* params, float* grads) {
+    if (!N) return set_error(HEC_ERR_INVALID_ARG, "net_get_params: NULL");
+    const size_t np = (size_t)NL * PSZ;
+    if (params) HEC_CUDA(cudaMemcpy(params, N->P, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    if (grads) HEC_CUDA(cudaMemcpy(grads, N->G, sizeof(float) * np, cudaMemcpyDeviceToHost));
+    return HEC_OK;
+}
+
+HEC_API hec_status net_set_params(hec_net* N, const float* params) {
+    if (!N || !params) return set_error(HEC_ERR_INVALID_ARG, "net_set_params: NULL");
+    HEC_CUDA(cudaMemcpy(N->P, params, sizeof(float) * (size_t)NL * PSZ, cudaMemcpyHostToDevice));
+    HEC_CHECK(refresh_weights(N, 0));
+    HEC_CUDA(cudaDeviceSynchronize());
+    return HEC_OK;
+}
+
+HEC_API hec_status net_forward(hec_net* N, int nx, int ny, int nz, int zs, const void* x_in, void* acts_out,
+                               float* out, void* stream) {
+    clear_error();
+    if (!N || !x_in) return set_error(HEC_ERR_INVALID_ARG, "net_forward: NULL");
+    Geom g{nx, ny, nz, zs};
+    HEC_CHECK(check_geom(g));
+    cudaStream_t s = S(stream);
+    const long nvox = (long)nx * ny * nz;
+    const dim3 grid = conv_grid(g);
+    HEC_CHECK(ensure(N, nvox, (long)grid.x * grid.y * grid.z));
+    HEC_CUDA(cudaMemcpyAsync(N->act[0], x_in, sizeof(__nv_bfloat16) * C * nvox, cudaMemcpyDeviceToDevice, s));
+    HEC_CHECK(forward(N, g, 1.f, s));
+    if (acts_out)
+        for (int l = 1; l <= NL; ++l)
+            HEC_CUDA(cudaMemcpyAsync((__nv_bfloat16*)acts_out + (long)(l - 1) * nvox * C, N->act[l],
+                                     sizeof(__nv_bfloat16) * C * nvox, cudaMemcpyDeviceToDevice, s));
+    if (out) HEC_CUDA(cudaMemcpyAsync(out, N->out, sizeof(float) * nvox, cudaMemcpyDeviceToDevice, s));
+    return HEC_OK;
+}
+
+HEC_API hec_status net_train_step(hec_net* N, int nx, int ny, int nz, int zs, const void* x_in, const float* target,
+                                  float lr, int update, float* loss_out, void* stream) {
+    clear_error();
+    if (!N || !x_in || !target) return set_error(HEC_ERR_INVALID_ARG, "net_train_step: NULL");
+    Geom g{nx, ny, nz, zs};
+    HEC_CHECK(check_geom(g));
+    cudaStream_t s = S(stream);
+    const long nvox = (long)nx * ny * nz;
+    const dim3 grid = conv_grid(g);
+    HEC_CHECK(ensure(N, nvox, (long)grid.x * grid.y * grid.z));
+    HEC_CUDA(cudaMemcpyAsync(N->act[0], x_in, sizeof(__nv_bfloat16) * C * nvox, cudaMemcpyDeviceToDevice, s));
+    HEC_CHECK(forward(N, g, 1.f, s));
+    const int lb = 1024;
+    k_mse<<<lb, 256, 0, s>>>(nvox, N->out, target, 1.f / (float)nvox, N->dA[0], N->lpart);
+    count_launch();
+    HEC_CHECK(backward(N, g, s));
+    if (update) {
+        N->step++;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - powf(b1, (float)N->step), c2 = 1.f - powf(b2, (float)N->step);
+        k_adam<<<(NL * PSZ + 255) / 256, 256, 0, s>>>(NL * PSZ, N->P, N->G, N->M, N->V, lr, b1, b2, 1e-8f, c1, c2);
+        count_launch();
+        HEC_CHECK(refresh_weights(N, s));
+    }
+    if (loss_out) {
+        std::vector<float> h(lb);
+        HEC_CUDA(cudaMemcpyAsync(h.data(), N->lpart, sizeof(float) * lb, cudaMemcpyDeviceToHost, s));
+        HEC_CUDA(cudaStreamSynchronize(s));
+        double t = 0.0;
+        for (float v : h) t += v;
+        *loss_out = (float)(t / (double)nvox);
+    }
+    HEC_CUDA(cudaGetLastError());
+    return HEC_OK;
+}

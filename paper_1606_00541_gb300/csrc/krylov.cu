@@ -390,9 +390,143 @@ hec_status spmv_impl(const hec_matrix* A, int K, double alpha, const double* x, 
     return go(std::integral_constant<int, 16>());
 }
 
+// ---- learned correction stage --------------------------------------------------------------
+hec_status net_apply_field(hec_net* N, int nx, int ny, int nz, const double* r, const double* sigma,
+                           const __nv_bfloat16* aux, cudaStream_t s);
+const float* net_output(const hec_net* N);
+
+namespace {
+__global__ void k_f64_to_bf16_scaled(long n, const double* __restrict__ a, double scale, __nv_bfloat16* __restrict__ o) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        o[i] = __float2bfloat16_rn((float)(a[i] * scale));
+}
+// sigma = sqrt(sum r^2 / n)
+__global__ void k_sigma(double* scal, long n) {
+    if (threadIdx.x == 0) scal[0] = sqrt(fmax(scal[1], 0.0) / (double)n);
+}
+__global__ void k_scale_out(long n, const float* __restrict__ out, const double* __restrict__ scal, double* __restrict__ c) {
+    const double s = scal[0];
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        c[i] = s * (double)out[i];
+}
+// alpha = <r1, Ac> / <Ac, Ac>; accepted when alpha > 0 and ||r1 - alpha Ac||^2 < rho^2 ||r1||^2
+__global__ void k_stage_decide(double* scal, double rho, long n, int* counters) {
+    if (threadIdx.x != 0) return;
+    const double rac = scal[2], acac = scal[3], rr = scal[1];
+    double coef = 0.0;
+    if (acac > 0.0) {
+        const double alpha = rac / acac;
+        const double left = rr - alpha * rac;  // ||r1 - alpha Ac||^2 at the optimal alpha
+        if (alpha > 0.0 && left < rho * rho * rr) coef = alpha;
+    }
+    scal[4] = coef;
+    counters[0] += 1;
+    if (coef != 0.0) counters[1] += 1;
+}
+__global__ void k_axpy_dev(long n, const double* __restrict__ coef, const double* __restrict__ c, double* __restrict__ z) {
+    const double a = *coef;
+    if (a == 0.0) return;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        z[i] = fma(a, c[i], z[i]);
+}
+}  // namespace
+
+}  // namespace hec
+
+// The stage: z = z1 + alpha c, c = sigma * Net([r1 / sigma, aux]), r1 = v - A z1 (z1 = the ILU
+// sweep's output); plain z1 whenever the correction does not reduce ||r1|| by the factor rho.
+struct hec_stage {
+    hec_net* net = nullptr;
+    const hec_matrix* A = nullptr;
+    int nx = 0, ny = 0, nz = 0;
+    double rho = 0.99;
+    __nv_bfloat16* aux = nullptr;  // [n] second input channel
+    double* work = nullptr;        // [3n]: r1 | Ac | c
+    double* scal = nullptr;        // sigma, ||r1||^2, <r1,Ac>, <Ac,Ac>, coef
+    int* counters = nullptr;       // applications, accepted corrections
+    hec::Dots* dots = nullptr;
+};
+
+namespace hec {
+hec_status stage_apply(const hec_stage* S, const double* v, double* z, cudaStream_t s) {
+    const int n = S->A->n;
+    double* r1 = S->work;
+    double* Ac = S->work + n;
+    double* c = S->work + 2 * (long)n;
+    const int gb = grid_for(n);
+    HEC_CUDA(cudaMemcpyAsync(r1, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    HEC_CHECK(spmv_impl(S->A, 1, -1.0, z, 1, 1.0, r1, 1, s));                     // r1 = v - A z1
+    HEC_CHECK(S->dots->run(n, 1, r1, n, 0, 1, r1, S->scal + 1, nullptr, s));      // ||r1||^2
+    k_sigma<<<1, 32, 0, s>>>(S->scal, n);
+    count_launch();
+    HEC_CHECK(net_apply_field(S->net, S->nx, S->ny, S->nz, r1, S->scal, S->aux, s));
+    k_scale_out<<<gb, kThreads, 0, s>>>(n, net_output(S->net), S->scal, c);       // c = sigma * Net
+    count_launch();
+    HEC_CHECK(spmv_impl(S->A, 1, 1.0, c, 1, 0.0, Ac, 1, s));                      // Ac
+    HEC_CHECK(S->dots->run(n, 1, S->work, n, 2, 0, Ac, S->scal + 2, nullptr, s));  // <r1,Ac>, <Ac,Ac>
+    k_stage_decide<<<1, 32, 0, s>>>(S->scal, S->rho, n, S->counters);
+    k_axpy_dev<<<gb, kThreads, 0, s>>>(n, S->scal + 4, c, z);
+    count_launch(2);
+    HEC_CUDA(cudaGetLastError());
+    return HEC_OK;
+}
 }  // namespace hec
 
 using namespace hec;
+
+HEC_API hec_status stage_create(hec_net* net, const hec_matrix* A, int nx, int ny, int nz, const double* aux,
+                                double aux_scale, double rho, hec_stage** out) {
+    clear_error();
+    if (!net || !A || !out || A->tri || A->vdt != HEC_F64 || (long)nx * ny * nz != A->n || !aux || !(rho > 0.0))
+        return set_error(HEC_ERR_INVALID_ARG, "stage_create: need the FP64 general-mode A on an nx*ny*nz grid");
+    *out = nullptr;
+    hec_stage* S = new hec_stage();
+    S->net = net;
+    S->A = A;
+    S->nx = nx;
+    S->ny = ny;
+    S->nz = nz;
+    S->rho = rho;
+    S->dots = new Dots();
+    const long n = A->n;
+    hec_status st = HEC_OK;
+    auto fail = [&](hec_status e) {
+        cudaFree(S->aux); cudaFree(S->work); cudaFree(S->scal); cudaFree(S->counters);
+        delete S->dots;
+        delete S;
+        return e;
+    };
+    if ((st = dalloc(&S->aux, (size_t)n)) || (st = dalloc(&S->work, (size_t)3 * n)) || (st = dalloc(&S->scal, 8)) ||
+        (st = dalloc(&S->counters, 2)) || (st = S->dots->init(3, 1)))
+        return fail(st);
+    k_f64_to_bf16_scaled<<<grid_for(n), kThreads>>>(n, aux, aux_scale, S->aux);
+    count_launch();
+    if (cudaMemset(S->counters, 0, 2 * sizeof(int)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return fail(cuda_error(cudaGetLastError(), "stage_create"));
+    *out = S;
+    return HEC_OK;
+}
+
+HEC_API hec_status stage_stats(const hec_stage* S, int* applied, int* accepted, int reset) {
+    if (!S) return set_error(HEC_ERR_INVALID_ARG, "stage_stats: NULL");
+    int h[2] = {0, 0};
+    HEC_CUDA(cudaMemcpy(h, S->counters, sizeof(h), cudaMemcpyDeviceToHost));
+    if (applied) *applied = h[0];
+    if (accepted) *accepted = h[1];
+    if (reset) HEC_CUDA(cudaMemset(S->counters, 0, sizeof(h)));
+    return HEC_OK;
+}
+
+HEC_API hec_status stage_destroy(hec_stage* S) {
+    if (!S) return HEC_OK;
+    cudaFree(S->aux);
+    cudaFree(S->work);
+    cudaFree(S->scal);
+    cudaFree(S->counters);
+    delete S->dots;
+    delete S;
+    return HEC_OK;
+}
 
 HEC_API hec_status spmv(const hec_matrix* A, int nrhs, double alpha, const double* x, int ldx, double beta, double* y,
                         int ldy, void* stream) {
@@ -424,14 +558,15 @@ struct FgmresWork {
 };
 }  // namespace
 
-HEC_API hec_status fgmres_solve(const hec_matrix* A, const ilu_precond* M, int nrhs, const double* b, int ldb,
-                                double* x, int ldx, int restart, double rtol, int max_iters, hec_fgmres_info* info,
-                                void* stream) {
+HEC_API hec_status fgmres_solve(const hec_matrix* A, const ilu_precond* M, const hec_stage* extra, int nrhs,
+                                const double* b, int ldb, double* x, int ldx, int restart, double rtol, int max_iters,
+                                hec_fgmres_info* info, void* stream) {
     clear_error();
     auto t_start = std::chrono::steady_clock::now();
     if (!A || A->tri || A->vdt != HEC_F64 || nrhs < 1 || nrhs > 16 || ldb < nrhs || ldx < nrhs || restart < 1 ||
-        restart > 256 || !(rtol > 0) || max_iters < 0 || (M && (M->n_glob != A->n || M->max_nrhs < nrhs)))
-        return set_error(HEC_ERR_INVALID_ARG, "fgmres_solve: bad argument");
+        restart > 256 || !(rtol > 0) || max_iters < 0 || (M && (M->n_glob != A->n || M->max_nrhs < nrhs)) ||
+        (extra && (!M || nrhs != 1 || extra->A->n != A->n)))
+        return set_error(HEC_ERR_INVALID_ARG, "fgmres_solve: bad argument (a learned stage needs M and nrhs = 1)");
     cudaStream_t s = S(stream);
     const int n = A->n, K = nrhs, m = restart;
     const long nk = (long)n * K;
@@ -539,6 +674,7 @@ HEC_API hec_status fgmres_solve(const hec_matrix* A, const ilu_precond* M, int n
             double* wv = W.V + (long)(j + 1) * nk;
             if (M) {
                 HEC_CHECK(ilu_apply(M, K, vj, K, zj, K, stream));
+                if (extra) HEC_CHECK(stage_apply(extra, vj, zj, s));
             } else {
                 HEC_CUDA(cudaMemcpyAsync(zj, vj, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
             }

@@ -78,7 +78,8 @@ _ilu_create = _sig("ilu_create", _vp, _vp, _i, _i, _vp, _vp, ctypes.POINTER(_vp)
 _ilu_destroy = _sig("ilu_destroy", _vp)
 _ilu_apply = _sig("ilu_apply", _vp, _i, _vp, _i, _vp, _i, _vp)
 _spmv = _sig("spmv", _vp, _i, _d, _vp, _i, _d, _vp, _i, _vp)
-_fgmres_solve = _sig("fgmres_solve", _vp, _vp, _i, _vp, _i, _vp, _i, _i, _d, _i, ctypes.POINTER(HecFgmresInfo), _vp)
+_fgmres_solve = _sig("fgmres_solve", _vp, _vp, _vp, _i, _vp, _i, _vp, _i, _i, _d, _i, ctypes.POINTER(HecFgmresInfo),
+                     _vp)
 _hec_csr_get = _sig("hec_csr_get", _vp, ctypes.POINTER(_i), ctypes.POINTER(_ll), ctypes.POINTER(_vp),
                     ctypes.POINTER(_vp), ctypes.POINTER(_vp))
 _hec_csr_destroy = _sig("hec_csr_destroy", _vp)
@@ -364,13 +365,15 @@ def spmv(A, x, y=None, alpha=1.0, beta=0.0, stream=None):
     return y
 
 
-def fgmres_solve(A, M, b, x=None, restart=30, rtol=1e-8, max_iters=1000, stream=None, raise_on_nonconvergence=True):
+def fgmres_solve(A, M, b, x=None, restart=30, rtol=1e-8, max_iters=1000, stream=None, raise_on_nonconvergence=True,
+                 stage=None):
     nrhs = _nrhs(b)
     if x is None:
         x = torch.zeros_like(b)
     info = HecFgmresInfo()
-    st = _fgmres_solve(A.h, M.h if M is not None else None, nrhs, _ptr(b), _ld(b, nrhs), _ptr(x), _ld(x, nrhs),
-                       int(restart), float(rtol), int(max_iters), ctypes.byref(info), _stream(stream))
+    st = _fgmres_solve(A.h, M.h if M is not None else None, stage.h if stage is not None else None, nrhs, _ptr(b),
+                       _ld(b, nrhs), _ptr(x), _ld(x, nrhs), int(restart), float(rtol), int(max_iters),
+                       ctypes.byref(info), _stream(stream))
     if st != OK and not (st == NOT_CONVERGED and not raise_on_nonconvergence):
         raise HecError(st, "fgmres_solve")
     return x, dict(iterations=info.iterations, restarts=info.restarts, converged=bool(info.converged),
@@ -383,6 +386,83 @@ def ilu_factor(rowptr, col, val, k=0, stream=None):
     _check(_ilu_factor(n, _ptr(rowptr), _ptr(col), _ptr(val), int(k), ctypes.byref(L), ctypes.byref(U), _stream(stream)),
            "ilu_factor")
     return Csr(L.value), Csr(U.value)
+
+
+_lib.net_param_count.restype = _i
+_net_create = _sig("net_create", _vp, ctypes.POINTER(_vp))
+_net_destroy = _sig("net_destroy", _vp)
+_net_get_params = _sig("net_get_params", _vp, _vp, _vp)
+_net_set_params = _sig("net_set_params", _vp, _vp)
+_net_forward = _sig("net_forward", _vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp)
+_net_train_step = _sig("net_train_step", _vp, _i, _i, _i, _i, _vp, _vp, ctypes.c_float, _i,
+                       ctypes.POINTER(ctypes.c_float), _vp)
+_stage_create = _sig("stage_create", _vp, _vp, _i, _i, _i, _vp, _d, _d, ctypes.POINTER(_vp))
+_stage_stats = _sig("stage_stats", _vp, ctypes.POINTER(_i), ctypes.POINTER(_i), _i)
+_stage_destroy = _sig("stage_destroy", _vp)
+
+
+def net_param_count():
+    return _lib.net_param_count()
+
+
+class Net(_Handle):
+    """The correction network (include/hec.h, learned stage).  params: numpy float32 array."""
+    _destroy = staticmethod(_net_destroy)
+
+    def __init__(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == net_param_count()
+        out = _vp()
+        _check(_net_create(p.ctypes.data_as(_vp), ctypes.byref(out)), "net_create")
+        super().__init__(out.value)
+
+    def params(self, grads=False):
+        import numpy as np
+        p = np.zeros(net_param_count(), dtype=np.float32)
+        g = np.zeros_like(p)
+        _check(_net_get_params(self.h, p.ctypes.data_as(_vp), g.ctypes.data_as(_vp)), "net_get_params")
+        return (p, g) if grads else p
+
+    def set_params(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(_net_set_params(self.h, p.ctypes.data_as(_vp)), "net_set_params")
+
+    def forward(self, x_in, dims, zs=None, acts=False, stream=None):
+        """x_in: CUDA bfloat16 tensor [nvox, 16]; dims = (nx, ny, nz).  Returns the FP32 output
+        [nvox] (and the BF16 layer outputs [4, nvox, 16] when acts)."""
+        nx, ny, nz = dims
+        nvox = nx * ny * nz
+        out = torch.empty(nvox, dtype=torch.float32, device="cuda")
+        a = torch.empty(4, nvox, 16, dtype=torch.bfloat16, device="cuda") if acts else None
+        _check(_net_forward(self.h, nx, ny, nz, zs or nz, _ptr(x_in), _ptr(a) if acts else None, _ptr(out),
+                            _stream(stream)), "net_forward")
+        return (out, a) if acts else out
+
+    def train_step(self, x_in, target, dims, zs=None, lr=1e-3, update=True, stream=None):
+        nx, ny, nz = dims
+        loss = ctypes.c_float()
+        _check(_net_train_step(self.h, nx, ny, nz, zs or nz, _ptr(x_in), _ptr(target), float(lr), 1 if update else 0,
+                               ctypes.byref(loss), _stream(stream)), "net_train_step")
+        return loss.value
+
+
+class Stage(_Handle):
+    """Learned correction stage for fgmres_solve (include/hec.h)."""
+    _destroy = staticmethod(_stage_destroy)
+
+    def __init__(self, net, A, dims, aux, aux_scale=0.5, rho=0.99):
+        out = _vp()
+        nx, ny, nz = dims
+        _check(_stage_create(net.h, A.h, nx, ny, nz, _ptr(aux), float(aux_scale), float(rho), ctypes.byref(out)),
+               "stage_create")
+        super().__init__(out.value, keep=(net, A))
+
+    def stats(self, reset=False):
+        a, b = _i(), _i()
+        _check(_stage_stats(self.h, ctypes.byref(a), ctypes.byref(b), 1 if reset else 0), "stage_stats")
+        return dict(applied=a.value, accepted=b.value)
 
 
 _ras_setup = _sig("ras_setup", _i, _vp, _vp, _vp, _vp, _i, ctypes.POINTER(_vp), _vp)
