@@ -165,6 +165,7 @@ def main():
     ap.add_argument("--size", type=int, default=128)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cfg4", action="store_true", help="also run the 200^3 learned-stage comparison")
     ap.add_argument("--ref-iters", type=int, default=150, help="iteration count used to scale the oracle sample")
     ap.add_argument("--ref-sample-iters", type=int, default=8)
     args = ap.parse_args()
@@ -286,6 +287,9 @@ def main():
 
     if rank == 0 and not args.no_variants:
         line["variants"] = variants(hec, torch, Ad, L, U, bd, HA0, n, nnzL, nnzU, hbm)
+        line["variants"]["learned_%d" % m] = learned_variant(hec, torch, m)
+        if args.cfg4:
+            line["variants"]["learned_200"] = learned_variant(hec, torch, 200)
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
             setup, per_it, fac = oracle_sample(A, bd.cpu().numpy(), args.ref_sample_iters)
@@ -339,6 +343,41 @@ def variants(hec, torch, Ad, L, U, bd, HA0, n, nnzL, nnzU, hbm):
                     "levels_U": s.lvU.nlev}
     out.update(batched_variants(hec, torch, Ad, L, U, n, hbm))
     return out
+
+
+def learned_variant(hec, torch, m, seed=0, crop=32, crops=125, epochs=8, log=None):
+    """ILU(0)-FGMRES(30) with and without the learned correction stage on the m^3 log-normal
+    7-point problem (FP32 factor values).  The network is trained from scratch on 2000 (residual,
+    error) pairs (125 crops of crop^3 from the same permeability field x 16 seeded right-hand
+    sides) generated by the FP64 solver; data generation and training times are reported apart."""
+    from paper_1606_00541_gb300 import learn, synth
+    lnk = np.log(synth.lognormal_perm(m, 2.0, seed))
+    A = synth.fv7_lognormal(m, perm=np.exp(lnk))
+    net, tinfo = learn.train_stage(lnk, m, crop=crop, crops=crops, rhs_per_crop=16, epochs=epochs, batch=8, lr=2e-3,
+                                   seed=seed + 1, log=log)
+    Ad = [torch.as_tensor(a, device="cuda") for a in A]
+    Lh, Uh = hec.ilu_factor(*Ad, k=0)
+    s = hec.IluSolver(Lh.tensors(), Uh.tensors(), A=Ad, vdt="f32")
+    b = hec.spmv(s.A, torch.as_tensor(synth.uniform_vector(m ** 3, seed + 1), device="cuda"))
+    stage = hec.Stage(net, s.A, (m, m, m), torch.as_tensor(lnk, device="cuda"), rho=0.99)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {"train": tinfo}
+    for name, st in (("plain", None), ("learned", stage)):
+        hec.fgmres_solve(s.A, s.M, b, stage=st, restart=RESTART, rtol=RTOL, max_iters=5000)  # warm
+        if st is not None:
+            st.stats(reset=True)
+        torch.cuda.synchronize()
+        e0.record()
+        x, info = hec.fgmres_solve(s.A, s.M, b, stage=st, restart=RESTART, rtol=RTOL, max_iters=5000)
+        e1.record()
+        torch.cuda.synchronize()
+        rel = float(torch.linalg.norm(b - hec.spmv(s.A, x)) / torch.linalg.norm(b))
+        res[name] = {"time_to_1e-8_s": e0.elapsed_time(e1) / 1000.0, "iterations": info["iterations"],
+                     "converged": info["converged"], "true_rel_residual": rel}
+        if st is not None:
+            res[name]["stage"] = st.stats()
+    res["n"] = m ** 3
+    return res
 
 
 def ras_cuts(m):
