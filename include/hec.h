@@ -184,6 +184,20 @@ hec_status sptrsv_lower(const sptrsv_plan* p, int nrhs, const double* b, int ldb
 hec_status sptrsv_upper(const sptrsv_plan* p, int nrhs, const double* b, int ldb, double* x,
                         int ldx, void* stream);
 
+/* Partitioned sweep (a GB300 schedule of Alg. 2's level loop, same results up to summation
+ * order): the rows are split into nparts parts, one thread block per part (all resident, so
+ * nparts <= sptrsv_partition_capacity()).  A block takes its rows level by level in the global
+ * level order with a block barrier between its levels; a dependency on a row of the same part
+ * is then a plain load, and only dependencies on other parts wait point to point through L2.
+ * part: device int[n], the part of each ORIGINAL row (compact regions of the grid work best; the
+ * paper partitions with METIS), or NULL for contiguous ranges of the original row index.
+ * threads: 128 or 256 (0 = 256) per block.  Applies to single-right-hand-side sweeps of this
+ * plan (sptrsv_lower / sptrsv_upper / ilu_apply with nrhs = 1); nparts = 0 removes it.  The plan
+ * keeps its own copy of the factor in the partitioned order.  Synchronizes `stream`. */
+hec_status sptrsv_plan_partition(sptrsv_plan* p, const int* part, int nparts, int threads,
+                                 void* stream);
+int sptrsv_partition_capacity(const sptrsv_plan* p, int threads);
+
 /* Autotuner: times the plan's own sweep (on a zero right-hand side, nrhs columns) for the
  * candidate launch shapes block_threads in {128, 256} x blocks_per_sm in {2, 4, 8, 16} (those that
  * fit 2048 threads per SM) and stores the fastest in the plan; `out` (host, may be NULL) receives

@@ -90,7 +90,29 @@ struct hec_matrix {
     const hec_levels* lv = nullptr;  // analysis used to pack (borrowed), NULL in general mode
 };
 
+// Partitioned layout of a plan (see sweep.cu, "partitioned sweep"): rows in (part, level,
+// global level order) order, the factor repacked in that order.
+struct hec_part_data {
+    int nparts = 0, nseg = 0;
+    int* rowg = nullptr;       // [n] plan row -> row of the level-ordered factor
+    int* part_row = nullptr;   // [nparts+1]
+    int* part_seg = nullptr;   // [nparts+1]
+    int* seg_start = nullptr;  // [nseg+1] first plan row of each (part, level) segment
+    int* ell_col = nullptr;    // repacked HEC (columns in plan numbering)
+    void* ell_val = nullptr;
+    int* tptr = nullptr;
+    int* tcol = nullptr;
+    void* tval = nullptr;
+    void* dinv = nullptr;
+    int* part_chunk = nullptr;  // [nparts+1] first level-aligned chunk of each part
+    int2* chunks = nullptr;     // (first plan row, rows <= 32)
+    int nchunks = 0;
+    int max_rows = 0;           // rows of the largest part (its shared-memory solution)
+    int threads = 256;
+};
+
 struct sptrsv_plan {
+    hec_part_data* part = nullptr;  // set by sptrsv_plan_partition
     const hec_matrix* T = nullptr;
     const hec_levels* lv = nullptr;
     int max_nrhs = 1;

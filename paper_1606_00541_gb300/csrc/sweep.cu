@@ -16,7 +16,9 @@
 // right-hand sides of a row interleaved, so one slab entry serves up to 16 solves.
 #include <algorithm>
 #include <mutex>
+#include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "internal.cuh"
 #include "sync.cuh"
@@ -448,6 +450,186 @@ __global__ void __launch_bounds__(256) k_sweep_vec(SweepParams p) {
     }
 }
 
+// ---- partitioned sweep ---------------------------------------------------------------------
+// The rows are split into parts, one resident CTA per part.  Inside a part the rows keep the
+// global level order and are cut into level-aligned chunks of at most 32 rows; chunk c of the
+// part goes to warp c mod (warps per CTA), so, as in the plain sweep, each row waits point to
+// point for exactly its dependencies and warps run ahead to later levels.  The part's own
+// solution values live in shared memory (sentinel-filled at start, the value is its own flag),
+// so a dependency inside the part is an SM-local poll of a few tens of cycles; only a dependency
+// on another part polls the global solution through L2.  With parts that are compact regions of
+// the grid, a long dependency chain crosses a part boundary only a few times.  Every wait is on
+// a row of lower global level and every warp walks its rows in increasing level, so the lowest
+// unfinished row can always proceed (all CTAs are resident: cooperative launch).
+struct PartParams {
+    int n, ld, w;
+    const int* __restrict__ ell_col;
+    const void* __restrict__ ell_val;
+    const int* __restrict__ tptr;
+    const int* __restrict__ tcol;
+    const void* __restrict__ tval;
+    const void* __restrict__ dinv;
+    const int* __restrict__ rowg;
+    const int* __restrict__ part_row;
+    const int* __restrict__ part_chunk;
+    const int2* __restrict__ chunks;
+    const double* __restrict__ b;
+    int ldb;
+    const int* __restrict__ gather;
+    double* __restrict__ x;
+    int ldx;
+    const int* __restrict__ scatter;
+    void* xp;
+    int* status;
+    long long budget;
+    int skip_row;
+};
+
+// dependencies of one lane, each either in this part's shared memory or in the global solution
+template <typename XT, typename AT, int NS>
+struct DepBatchP {
+    typedef Word<XT> W;
+    typedef typename W::T WT;
+    const WT* addr[NS];
+    WT raw[NS];
+    AT v[NS];
+    unsigned valid, pend, local;
+    __device__ __forceinline__ void clear() {
+        valid = pend = local = 0;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            addr[k] = nullptr;
+            raw[k] = 0;
+            v[k] = AT(0);
+        }
+    }
+    __device__ __forceinline__ void set(int k, const XT* xp, const WT* sxp, int cc, int lo, int hi, AT coef) {
+        v[k] = coef;
+        valid |= 1u << k;
+        pend |= 1u << k;
+        if (cc >= lo && cc < hi) {
+            addr[k] = sxp + (cc - lo);
+            local |= 1u << k;
+        } else {
+            addr[k] = (const WT*)(xp + cc);
+        }
+    }
+    __device__ __forceinline__ void poll() {
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            if (pend & (1u << k)) {
+                raw[k] = (local & (1u << k)) ? *(const volatile WT*)addr[k] : W::load((const XT*)addr[k]);
+                if (raw[k] != W::kSent) pend &= ~(1u << k);
+            }
+        }
+    }
+    __device__ __forceinline__ void wait(int* status, long long budget) {
+        if (!__any_sync(kFull, pend)) return;
+        const long long t0 = clock64();
+        for (unsigned it = 1;; ++it) {
+            poll();
+            if (!__any_sync(kFull, pend)) return;
+            if ((it & 63u) == 0u) {
+                bool give_up = (clock64() - t0 > budget) || (ld_relaxed_u32(status) != 0u);
+                if (__any_sync(kFull, give_up)) {
+                    record(status, HEC_ERR_TIMEOUT);
+#pragma unroll
+                    for (int k = 0; k < NS; ++k)
+                        if (pend & (1u << k)) raw[k] = 0;
+                    return;
+                }
+            }
+        }
+    }
+    __device__ __forceinline__ AT accumulate(AT acc) const {
+#pragma unroll
+        for (int k = 0; k < NS; ++k)
+            if (valid & (1u << k)) acc = fma(-v[k], (AT)W::val(raw[k]), acc);
+        return acc;
+    }
+};
+
+template <typename VT, typename XT, int WMAX>
+__global__ void __launch_bounds__(256) k_sweep_part(PartParams p) {
+    typedef typename Acc<XT>::T AT;
+    typedef Word<XT> W;
+    typedef typename W::T WT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WT* sxp = (WT*)smem_raw;
+    const int part = blockIdx.x;
+    const int lo = __ldg(p.part_row + part), hi = __ldg(p.part_row + part + 1);
+    for (int i = threadIdx.x; i < hi - lo; i += blockDim.x) sxp[i] = W::kSent;
+    __syncthreads();
+    const int c0 = __ldg(p.part_chunk + part), c1 = __ldg(p.part_chunk + part + 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const VT* __restrict__ ev = (const VT*)p.ell_val;
+    const VT* __restrict__ tv = (const VT*)p.tval;
+    XT* xp = (XT*)p.xp;
+    for (int c = c0 + warp; c < c1; c += nwarps) {
+        const int2 ch = __ldg(p.chunks + c);
+        const int r = ch.x + lane;
+        const bool act = lane < ch.y;
+        AT acc = AT(0), diag = AT(1);
+        int t0 = 0, tl = 0, sr = -1;
+        if (act) {
+            const int g = __ldg(p.rowg + r);
+            const int gr = p.gather ? __ldg(p.gather + g) : g;
+            acc = (AT)__ldg(p.b + (long)gr * p.ldb);
+            t0 = __ldg(p.tptr + r);
+            tl = __ldg(p.tptr + r + 1) - 1 - t0;
+            diag = (AT)__ldg((const XT*)p.dinv + r);
+            sr = p.scatter ? __ldg(p.scatter + g) : g;
+        }
+        DepBatchP<XT, AT, WMAX> slab;
+        slab.clear();
+#pragma unroll
+        for (int k = 0; k < WMAX; ++k) {
+            if (act && k < p.w) {
+                const long s = (long)k * p.ld + r;
+                const int cc = __ldg(p.ell_col + s);
+                if (cc >= 0) slab.set(k, xp, sxp, cc, lo, hi, ldv<VT, AT>(ev + s));
+            }
+        }
+        const int tmax = __reduce_max_sync(kFull, tl);
+        slab.poll();
+        slab.wait(p.status, p.budget);
+        acc = slab.accumulate(acc);
+        for (int k = WMAX; k < p.w; ++k) {
+            DepBatchP<XT, AT, 1> one;
+            one.clear();
+            if (act) {
+                const long s = (long)k * p.ld + r;
+                const int cc = __ldg(p.ell_col + s);
+                if (cc >= 0) one.set(0, xp, sxp, cc, lo, hi, ldv<VT, AT>(ev + s));
+            }
+            one.poll();
+            one.wait(p.status, p.budget);
+            acc = one.accumulate(acc);
+        }
+        for (int tb = 0; tb < tmax; tb += kTailBatch) {
+            DepBatchP<XT, AT, kTailBatch> tail;
+            tail.clear();
+#pragma unroll
+            for (int k = 0; k < kTailBatch; ++k)
+                if (tb + k < tl)
+                    tail.set(k, xp, sxp, __ldg(p.tcol + t0 + tb + k), lo, hi, ldv<VT, AT>(tv + t0 + tb + k));
+            tail.poll();
+            tail.wait(p.status, p.budget);
+            acc = tail.accumulate(acc);
+        }
+        if (act) {
+            const AT xr = acc * diag;
+            WT wv = sizeof(XT) == 8 ? (WT)__double_as_longlong((double)(XT)xr) : (WT)__float_as_uint((float)(XT)xr);
+            if (wv == W::kSent) wv = sizeof(XT) == 8 ? (WT)0x7FF8000000000000ull : (WT)0x7FC00000u;
+            if (r != p.skip_row) {
+                *(volatile WT*)(sxp + (r - lo)) = wv;  // consumers in this part
+                publish_x(xp + r, (XT)xr);             // consumers in other parts
+            }
+            if (sr >= 0) p.x[(long)sr * p.ldx] = (double)xr;
+        }
+    }
+}
+
 template <typename XT>
 __global__ void k_fill_sentinel(XT* xp, long count) {
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -628,10 +810,76 @@ hec_status build_chunks(sptrsv_plan* p) {
 
 }  // namespace
 
+namespace {
+template <typename VT, typename XT, int WMAX>
+hec_status launch_part(const sptrsv_plan* pl, PartParams& pp, cudaStream_t s) {
+    const hec_part_data* P = pl->part;
+    const void* k = (const void*)k_sweep_part<VT, XT, WMAX>;
+    const long count = pl->T->n;
+    const int fb = (int)std::min(4096L, std::max(1L, (count + 255) / 256));
+    {
+        ProfScope ps_(s, PROF_FILL);
+        k_fill_sentinel<XT><<<fb, 256, 0, s>>>((XT*)pp.xp, count);
+    }
+    HEC_LAUNCHED();
+    void* args[] = {&pp};
+    void* tok = nullptr;
+    const size_t smem = (size_t)P->max_rows * sizeof(XT);
+    profile_begin(s, &tok);
+    HEC_CUDA(cudaLaunchCooperativeKernel(k, dim3(P->nparts), dim3(P->threads), args, smem, s));
+    profile_end(s, tok);
+    count_launch();
+    return HEC_OK;
+}
+
+template <typename VT, typename XT>
+hec_status dispatch_part(const sptrsv_plan* pl, PartParams& pp, cudaStream_t s) {
+    if (pp.w <= 4) return launch_part<VT, XT, 4>(pl, pp, s);
+    return launch_part<VT, XT, 8>(pl, pp, s);
+}
+
+template <typename VT, typename XT>
+const void* part_kernel(int w) {
+    return w <= 4 ? (const void*)k_sweep_part<VT, XT, 4> : (const void*)k_sweep_part<VT, XT, 8>;
+}
+}  // namespace
+
 hec_status sweep(const sptrsv_plan* pl, int nrhs, const double* b, int ldb, const int* gather, double* x, int ldx,
                  const int* scatter, cudaStream_t s) {
     const hec_matrix* T = pl->T;
     if (T->n == 0) return HEC_OK;
+    if (pl->part && nrhs == 1) {
+        const hec_part_data* P = pl->part;
+        PartParams pp;
+        pp.n = T->n;
+        pp.ld = T->ld;
+        pp.w = T->w;
+        pp.ell_col = P->ell_col;
+        pp.ell_val = P->ell_val;
+        pp.tptr = P->tptr;
+        pp.tcol = P->tcol;
+        pp.tval = P->tval;
+        pp.dinv = P->dinv;
+        pp.rowg = P->rowg;
+        pp.part_row = P->part_row;
+        pp.part_chunk = P->part_chunk;
+        pp.chunks = P->chunks;
+        pp.b = b;
+        pp.ldb = ldb;
+        pp.gather = gather;
+        pp.x = x;
+        pp.ldx = ldx;
+        pp.scatter = scatter;
+        pp.xp = pl->xp;
+        pp.status = pl->status;
+        pp.budget = pl->wait_cycles;
+        pp.skip_row = pl->skip_row;
+        switch (T->vdt) {
+            case HEC_F64: return dispatch_part<double, double>(pl, pp, s);
+            case HEC_F32: return dispatch_part<float, float>(pl, pp, s);
+            default: return dispatch_part<__nv_bfloat16, float>(pl, pp, s);
+        }
+    }
     SweepParams sp;
     sp.n = T->n;
     sp.ld = T->ld;
@@ -675,13 +923,230 @@ __global__ void k_ilu_maps(int n, const int* __restrict__ iperm_l, const int* __
 }
 }  // namespace
 
+void free_part(hec_part_data* P) {
+    if (!P) return;
+    cudaFree(P->rowg); cudaFree(P->part_row); cudaFree(P->part_seg); cudaFree(P->seg_start);
+    cudaFree(P->ell_col); cudaFree(P->ell_val); cudaFree(P->tptr); cudaFree(P->tcol); cudaFree(P->tval); cudaFree(P->dinv);
+    delete P;
+}
+
 void free_plan(sptrsv_plan* p) {
     if (!p) return;
     cudaFree(p->xp);
     cudaFree(p->status);
     for (int i = 0; i < 5; ++i) cudaFree(p->chunks[i]);
     cudaFree(p->dinv);
+    free_part(p->part);
     delete p;
+}
+
+hec_status sort_pairs_i32(int* keys, int* vals, int n, int max_key, cudaStream_t s);
+
+namespace {
+// part id of each level-ordered row g (from the caller's map of original rows, or contiguous
+// ranges of the original index), and the identity payload for the sort
+__global__ void k_part_keys(int n, const int* __restrict__ iperm, const int* __restrict__ part, int nparts, int* key,
+                            int* val, int* bad) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const int i = iperm[g];
+    const int pk = part ? part[i] : (int)((long long)i * nparts / n);
+    if (pk < 0 || pk >= nparts) atomicCAS(bad, 0, 1);
+    key[g] = min(max(pk, 0), nparts - 1);
+    val[g] = g;
+}
+__global__ void k_hist(int n, const int* __restrict__ key, int* cnt) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) atomicAdd(cnt + key[r], 1);
+}
+// segment starts: a new segment where the part or the level changes
+__global__ void k_seg_flags(int n, const int* __restrict__ key, const int* __restrict__ rowg,
+                            const int* __restrict__ iperm, const int* __restrict__ level, int* flag, int* sigma) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int g = rowg[r];
+    sigma[g] = r;
+    int f = 1;
+    if (r > 0) {
+        const int g0 = rowg[r - 1];
+        f = (key[r] != key[r - 1]) || (level[iperm[g]] != level[iperm[g0]]);
+    }
+    flag[r] = f;
+}
+__global__ void k_seg_table(int n, const int* __restrict__ flag, const int* __restrict__ segidx, int nseg, int* seg_start) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n && flag[r]) seg_start[segidx[r]] = r;
+    if (r == 0) seg_start[nseg] = n;
+}
+__global__ void k_part_seg(int nparts, int n, int nseg, const int* __restrict__ part_row, const int* __restrict__ segidx,
+                           int* part_seg) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > nparts) return;
+    const int r = part_row[p];
+    part_seg[p] = r < n ? segidx[r] : nseg;
+}
+__global__ void k_gather_idx(int m, const int* __restrict__ idx, const int* __restrict__ src, int* dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) dst[i] = src[idx[i]];
+}
+__global__ void k_tail_len_perm(int n, const int* __restrict__ rowg, const int* __restrict__ tptr, int* len) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) len[r] = tptr[rowg[r] + 1] - tptr[rowg[r]];
+}
+// plan row r takes level-ordered row g = rowg[r]; columns renumbered by sigma and re-sorted
+template <typename VT>
+__global__ void k_repack(int n, int ld, int w, const int* __restrict__ rowg, const int* __restrict__ sigma,
+                         const int* __restrict__ ec, const VT* __restrict__ ev, const int* __restrict__ tp,
+                         const int* __restrict__ tc, const VT* __restrict__ tv, const int* __restrict__ ntp, int* nec,
+                         VT* nev, int* ntc, VT* ntv) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ld) return;
+    if (r >= n) {
+        for (int k = 0; k < w; ++k) {
+            nec[(long)k * ld + r] = -1;
+            nev[(long)k * ld + r] = (VT)0.0f;
+        }
+        return;
+    }
+    const int g = rowg[r];
+    int nell = 0;
+    for (int k = 0; k < w; ++k) nell += ec[(long)k * ld + g] >= 0;
+    const int t0 = tp[g], tcnt = tp[g + 1] - t0 - 1;  // overflow entries, the diagonal excluded
+    const int cnt = nell + tcnt;
+    auto col_of = [&](int e) { return sigma[e < nell ? ec[(long)e * ld + g] : tc[t0 + e - nell]]; };
+    auto val_of = [&](int e) { return e < nell ? ev[(long)e * ld + g] : tv[t0 + e - nell]; };
+    const int nt0 = ntp[r];
+    for (int e = 0; e < cnt; ++e) {
+        const int c = col_of(e);
+        int rank = 0;
+        for (int f = 0; f < cnt; ++f) rank += col_of(f) < c;
+        if (rank < w) {
+            nec[(long)rank * ld + r] = c;
+            nev[(long)rank * ld + r] = val_of(e);
+        } else {
+            ntc[nt0 + rank - w] = c;
+            ntv[nt0 + rank - w] = val_of(e);
+        }
+    }
+    for (int k = cnt; k < w; ++k) {
+        nec[(long)k * ld + r] = -1;
+        nev[(long)k * ld + r] = (VT)0.0f;
+    }
+    ntc[ntp[r + 1] - 1] = r;
+    ntv[ntp[r + 1] - 1] = tv[tp[g + 1] - 1];
+}
+template <typename XT>
+__global__ void k_perm_dinv(int n, const int* __restrict__ rowg, const XT* __restrict__ d, XT* nd) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) nd[r] = d[rowg[r]];
+}
+}  // namespace
+
+hec_status build_partition(sptrsv_plan* p, const int* part, int nparts, cudaStream_t s) {
+    const hec_matrix* T = p->T;
+    const hec_levels* lv = p->lv;
+    const int n = T->n;
+    hec_part_data* P = new hec_part_data();
+    P->nparts = nparts;
+    int *key = nullptr, *flag = nullptr, *segidx = nullptr, *sigma = nullptr, *len = nullptr, *bad = nullptr;
+    hec_status st = HEC_OK;
+    auto done = [&](hec_status e) {
+        cudaFree(key); cudaFree(flag); cudaFree(segidx); cudaFree(sigma); cudaFree(len); cudaFree(bad);
+        if (e != HEC_OK) free_part(P);
+        return e;
+    };
+    const int g = (n + 255) / 256;
+    if ((st = dalloc(&key, n)) || (st = dalloc(&P->rowg, n)) || (st = dalloc(&bad, 1)) ||
+        (st = dalloc(&P->part_row, (size_t)nparts + 1)) || (st = dalloc(&flag, (size_t)n + 1)) ||
+        (st = dalloc(&segidx, (size_t)n + 1)) || (st = dalloc(&sigma, n)) || (st = dalloc(&len, (size_t)n + 1)) ||
+        (st = dalloc(&P->part_seg, (size_t)nparts + 1)))
+        return done(st);
+    cudaMemsetAsync(bad, 0, sizeof(int), s);
+    k_part_keys<<<g, 256, 0, s>>>(n, lv->iperm, part, nparts, key, P->rowg, bad);
+    count_launch();
+    int hbad = 0;
+    HEC_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HEC_CUDA(cudaStreamSynchronize(s));
+    if (hbad) return done(set_error(HEC_ERR_INVALID_ARG, "sptrsv_plan_partition: part[] outside [0, nparts)"));
+    if ((st = sort_pairs_i32(key, P->rowg, n, nparts - 1, s))) return done(st);
+    HEC_CUDA(cudaMemsetAsync(P->part_row, 0, sizeof(int) * ((size_t)nparts + 1), s));
+    k_hist<<<g, 256, 0, s>>>(n, key, P->part_row);
+    k_seg_flags<<<g, 256, 0, s>>>(n, key, P->rowg, lv->iperm, lv->level, flag, sigma);
+    count_launch(2);
+    if ((st = exclusive_scan_i32(P->part_row, P->part_row, nparts, true, s))) return done(st);
+    if ((st = exclusive_scan_i32(flag, segidx, n, true, s))) return done(st);
+    HEC_CUDA(cudaMemcpy(&P->nseg, segidx + n, sizeof(int), cudaMemcpyDeviceToHost));
+    if ((st = dalloc(&P->seg_start, (size_t)P->nseg + 1))) return done(st);
+    k_seg_table<<<g, 256, 0, s>>>(n, flag, segidx, P->nseg, P->seg_start);
+    k_part_seg<<<(nparts + 256) / 256, 256, 0, s>>>(nparts, n, P->nseg, P->part_row, segidx, P->part_seg);
+    k_tail_len_perm<<<g, 256, 0, s>>>(n, P->rowg, T->tptr, len);
+    count_launch(3);
+    if ((st = dalloc(&P->tptr, (size_t)n + 1)) || (st = exclusive_scan_i32(len, P->tptr, n, true, s))) return done(st);
+    // level-aligned chunks of at most 32 rows inside each (part, level) segment
+    {
+        int* cseg = nullptr;
+        if ((st = dalloc(&cseg, (size_t)P->nseg + 1)) || (st = dalloc(&P->part_chunk, (size_t)nparts + 1))) {
+            cudaFree(cseg);
+            return done(st);
+        }
+        k_chunk_counts<<<(P->nseg + 255) / 256, 256, 0, s>>>(P->nseg, P->seg_start, 32, cseg);
+        count_launch();
+        if ((st = exclusive_scan_i32(cseg, cseg, P->nseg, true, s))) { cudaFree(cseg); return done(st); }
+        cudaMemcpy(&P->nchunks, cseg + P->nseg, sizeof(int), cudaMemcpyDeviceToHost);
+        if ((st = dalloc(&P->chunks, (size_t)P->nchunks))) { cudaFree(cseg); return done(st); }
+        k_chunk_table<<<(P->nchunks + 255) / 256, 256, 0, s>>>(P->nseg, P->seg_start, cseg, 32, P->nchunks, P->chunks);
+        k_gather_idx<<<(nparts + 256) / 256, 256, 0, s>>>(nparts + 1, P->part_seg, cseg, P->part_chunk);
+        count_launch(2);
+        cudaError_t ce = cudaStreamSynchronize(s);
+        cudaFree(cseg);
+        if (ce != cudaSuccess) return done(cuda_error(ce, "partition chunks"));
+        std::vector<int> pr((size_t)nparts + 1);
+        HEC_CUDA(cudaMemcpy(pr.data(), P->part_row, sizeof(int) * pr.size(), cudaMemcpyDeviceToHost));
+        for (int q = 0; q < nparts; ++q) P->max_rows = std::max(P->max_rows, pr[q + 1] - pr[q]);
+    }
+    const size_t vs = T->vdt == HEC_F64 ? 8 : T->vdt == HEC_F32 ? 4 : 2;
+    const size_t ws = T->vdt == HEC_F64 ? 8 : 4;
+    if ((st = dalloc(&P->ell_col, (size_t)T->w * T->ld)) || (st = dmalloc(&P->ell_val, vs * (size_t)T->w * T->ld + 16)) ||
+        (st = dalloc(&P->tcol, (size_t)T->tail_nnz)) || (st = dmalloc(&P->tval, vs * (size_t)T->tail_nnz + 16)) ||
+        (st = dmalloc(&P->dinv, ws * (size_t)n + 16)))
+        return done(st);
+    const int gl = (T->ld + 255) / 256;
+    if (T->vdt == HEC_F64) {
+        k_repack<double><<<gl, 256, 0, s>>>(n, T->ld, T->w, P->rowg, sigma, T->ell_col, (const double*)T->ell_val, T->tptr,
+                                            T->tcol, (const double*)T->tval, P->tptr, P->ell_col, (double*)P->ell_val,
+                                            P->tcol, (double*)P->tval);
+        k_perm_dinv<double><<<g, 256, 0, s>>>(n, P->rowg, (const double*)p->dinv, (double*)P->dinv);
+    } else if (T->vdt == HEC_F32) {
+        k_repack<float><<<gl, 256, 0, s>>>(n, T->ld, T->w, P->rowg, sigma, T->ell_col, (const float*)T->ell_val, T->tptr,
+                                           T->tcol, (const float*)T->tval, P->tptr, P->ell_col, (float*)P->ell_val, P->tcol,
+                                           (float*)P->tval);
+        k_perm_dinv<float><<<g, 256, 0, s>>>(n, P->rowg, (const float*)p->dinv, (float*)P->dinv);
+    } else {
+        k_repack<__nv_bfloat16><<<gl, 256, 0, s>>>(n, T->ld, T->w, P->rowg, sigma, T->ell_col,
+                                                   (const __nv_bfloat16*)T->ell_val, T->tptr, T->tcol,
+                                                   (const __nv_bfloat16*)T->tval, P->tptr, P->ell_col,
+                                                   (__nv_bfloat16*)P->ell_val, P->tcol, (__nv_bfloat16*)P->tval);
+        k_perm_dinv<float><<<g, 256, 0, s>>>(n, P->rowg, (const float*)p->dinv, (float*)P->dinv);
+    }
+    count_launch(2);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return done(cuda_error(e, "sptrsv_plan_partition"));
+    free_part(p->part);
+    p->part = P;
+    return done(HEC_OK);
+}
+
+// resident blocks of the partitioned kernel for `smem` bytes of shared solution per block
+int part_capacity(const sptrsv_plan* p, int threads, size_t smem) {
+    const void* k = p->T->vdt == HEC_F64 ? part_kernel<double, double>(p->T->w)
+                    : p->T->vdt == HEC_F32 ? part_kernel<float, float>(p->T->w)
+                                           : part_kernel<__nv_bfloat16, float>(p->T->w);
+    if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return max_coop_blocks(k, threads, smem) * num_sms();
 }
 
 }  // namespace hec
@@ -718,6 +1183,51 @@ HEC_API hec_status sptrsv_plan_create(const hec_matrix* tri, const hec_levels* l
     if (st != HEC_OK) { free_plan(p); return st; }
     *out = p;
     return HEC_OK;
+}
+
+HEC_API hec_status sptrsv_plan_partition(sptrsv_plan* p, const int* part, int nparts, int threads, void* stream) {
+    clear_error();
+    if (!p) return set_error(HEC_ERR_INVALID_ARG, "sptrsv_plan_partition: NULL plan");
+    if (nparts == 0) {
+        free_part(p->part);
+        p->part = nullptr;
+        return HEC_OK;
+    }
+    if (threads == 0) threads = 256;
+    if (nparts < 1 || (threads != 128 && threads != 256) || p->T->n == 0)
+        return set_error(HEC_ERR_INVALID_ARG, "sptrsv_plan_partition: need nparts >= 1, threads 128 or 256");
+    const int cap0 = part_capacity(p, threads, 0);
+    if (nparts > cap0)
+        return set_error(HEC_ERR_INVALID_ARG, "sptrsv_plan_partition: " + std::to_string(nparts) +
+                                                  " parts cannot all be resident (at most " + std::to_string(cap0) + ")");
+    sptrsv_plan tmp;  // build into a scratch holder, keep the old partition on failure
+    tmp.T = p->T;
+    tmp.lv = p->lv;
+    tmp.dinv = p->dinv;
+    hec_status st = build_partition(&tmp, part, nparts, S(stream));
+    tmp.dinv = nullptr;
+    if (st != HEC_OK) return st;
+    const size_t ws = p->T->vdt == HEC_F64 ? 8 : 4;
+    const size_t smem = (size_t)tmp.part->max_rows * ws;
+    const int cap = smem <= 227 * 1024 ? part_capacity(p, threads, smem) : 0;
+    if (nparts > cap) {
+        free_part(tmp.part);
+        tmp.part = nullptr;
+        return set_error(HEC_ERR_INVALID_ARG, "sptrsv_plan_partition: the largest part (" +
+                                                  std::to_string(smem) + " bytes of shared solution) leaves room for " +
+                                                  std::to_string(cap) + " resident parts, fewer than " +
+                                                  std::to_string(nparts));
+    }
+    free_part(p->part);
+    p->part = tmp.part;
+    tmp.part = nullptr;
+    p->part->threads = threads;
+    return HEC_OK;
+}
+
+HEC_API int sptrsv_partition_capacity(const sptrsv_plan* p, int threads) {
+    if (!p) return 0;
+    return part_capacity(p, threads ? threads : 256, 0);
 }
 
 HEC_API hec_status sptrsv_plan_destroy(sptrsv_plan* p) {

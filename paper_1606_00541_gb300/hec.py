@@ -316,6 +316,23 @@ def _solve(fn, name, plan, b, x, stream):
     return x
 
 
+_sptrsv_plan_partition = _sig("sptrsv_plan_partition", _vp, _vp, _i, _i, _vp)
+_lib.sptrsv_partition_capacity.restype = _i
+_lib.sptrsv_partition_capacity.argtypes = [_vp, _i]
+
+
+def sptrsv_plan_partition(plan, part=None, nparts=0, threads=0, stream=None):
+    """Partitioned single-RHS sweeps (include/hec.h): part = CUDA int32 tensor [n] of part ids per
+    original row, or None for contiguous row ranges; nparts = 0 removes the partition."""
+    _check(_sptrsv_plan_partition(plan.h, _ptr(part) if part is not None else None, int(nparts), int(threads),
+                                  _stream(stream)), "sptrsv_plan_partition")
+    plan._part = part
+
+
+def sptrsv_partition_capacity(plan, threads=0):
+    return _lib.sptrsv_partition_capacity(plan.h, int(threads))
+
+
 _sptrsv_autotune = _sig("sptrsv_autotune", _vp, _i, ctypes.POINTER(HecTune), _vp)
 
 
@@ -522,6 +539,14 @@ class IluSolver:
         self.pU = sptrsv_plan_create(self.HU, self.lvU, max_nrhs, **tune)
         self.M = ilu_create(self.pL, self.pU)
         self.A = hec_from_csr(*A, vdt="f64", stream=stream) if A is not None else None
+
+    def partition(self, part=None, nparts=None, threads=0, stream=None):
+        """Partitioned single-RHS sweeps on both factors (default: as many contiguous parts as fit)."""
+        if nparts is None:
+            nparts = min(sptrsv_partition_capacity(self.pL, threads), sptrsv_partition_capacity(self.pU, threads))
+        sptrsv_plan_partition(self.pL, part, nparts, threads, stream)
+        sptrsv_plan_partition(self.pU, part, nparts, threads, stream)
+        return nparts
 
     def autotune(self, nrhs=1, stream=None):
         """Runs the sweep autotuner on both plans; returns the chosen launch shapes."""
