@@ -154,6 +154,24 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# --- replicas (one process per GPU, no collective on the data path) ----------------------------
+
+def max_over_ranks(x, device):
+    """The slowest rank's time: the job's time.  A no-op on one process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, steps, elapsed_max):
+    """Solves per second over all replicas: each rank solves `steps` independent systems."""
+    return world * steps / elapsed_max
+
+
 # --- our arm --------------------------------------------------------------------------------------
 
 def main():
@@ -229,11 +247,8 @@ def main():
     sweep_ms, sweep_launches = hec.profile_read(reset=True)
     hec.profile_enable(False)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([elapsed], device=devn)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = world * args.steps / elapsed
+    elapsed = max_over_ranks(elapsed, devn)
+    value = whole_job_value(world, args.steps, elapsed)
     its = infos[-1]["iterations"]
     xr = x
     res = bd - hec.spmv(HA0, xr)
@@ -268,10 +283,7 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     e2e_s = e0.elapsed_time(e1) / 1000.0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=devn)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, devn)
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * step_s, "higher_is_better": True, "scaling": "weak",
