@@ -1,0 +1,152 @@
+"""Parity at the workloads' full sizes, in the configuration bench.py times.
+
+The C oracle is fast enough to produce complete reference outputs here: ILU(0) and level sets of
+the 2M- and 8M-row matrices, ILUT of the 27-point 100^3 matrix, the RAS subdomain solves, and
+forward / back substitution.  Bars as in the small-case tests: integer outputs bit-exact, FP64
+sweeps within 1e-12, FGMRES true residual within 1e-8."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1606_00541_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hec():
+    from paper_1606_00541_gb300 import hec as h
+    return h
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def relmax(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def cfg1(hec):
+    m = 128
+    A = synth.fv7_lognormal(m, sigma=2.0, seed=0)
+    L, U = oracle.ilu0(A)
+    return m, A, L, U
+
+
+def test_cfg1_factor_levels_pack_and_sweeps(hec, cfg1):
+    m, A, L, U = cfg1
+    n = m ** 3
+    Ad = [dev(a) for a in A]
+    Lh, Uh = hec.ilu_factor(*Ad, k=0)
+    Lg, Ug = [[t.cpu().numpy() for t in h.tensors()] for h in (Lh, Uh)]
+    for got, exp in [(Lg, L), (Ug, U)]:
+        assert np.array_equal(got[0], exp[0]) and np.array_equal(got[1], exp[1])
+        assert relmax(got[2], exp[2]) <= 1e-12
+    b = synth.uniform_vector(n, 1)
+    for uplo, T in [(0, L), (1, U)]:
+        Td = [dev(a) for a in T]
+        lv = hec.sptrsv_analyze(Td[0], Td[1], uplo)
+        assert lv.nlev == 3 * m - 2
+        ref = oracle.analyze(T, uplo)
+        lev, perm, iperm, lp = [a.cpu().numpy() for a in lv.arrays()]
+        assert np.array_equal(lev, ref["level"]) and np.array_equal(perm, ref["perm"])
+        assert np.array_equal(lp, ref["level_ptr"])
+        for vdt in ["f64", "f32"]:
+            H = hec.hec_from_csr(*Td, levels=lv, vdt=vdt)
+            R = oracle.hec_pack(T, 1, uplo, ref["perm"], ref["iperm"], vdt=vdt)
+            arrs = H.arrays()
+            for key in ["ell_col", "tptr", "tcol"]:
+                assert np.array_equal(arrs[key].cpu().numpy(), R[key]), key
+            for key in ["ell_val", "tval"]:
+                got = arrs[key].cpu().numpy()
+                got = got.view(np.uint32) if vdt == "f32" else got
+                assert np.array_equal(got, R[key]), key
+        H = hec.hec_from_csr(*Td, levels=lv, vdt="f64")
+        p = hec.sptrsv_plan_create(H, lv, 1)
+        x = (hec.sptrsv_lower if uplo == 0 else hec.sptrsv_upper)(p, dev(b)).cpu().numpy()
+        xr = (oracle.lower_solve if uplo == 0 else oracle.upper_solve)(T, b)
+        assert relmax(x, xr) <= 1e-12
+
+
+def test_cfg1_fgmres_fp32_factors(hec, cfg1):
+    """The bench step's solve: FP32 factor values, FP64 FGMRES(30), 1e-8 true residual."""
+    m, A, L, U = cfg1
+    n = m ** 3
+    xt = synth.uniform_vector(n, 1)
+    b = oracle.spmv(A, xt)
+    s = hec.IluSolver([dev(a) for a in L], [dev(a) for a in U], A=[dev(a) for a in A], vdt="f32")
+    x, info = s.solve(dev(b), restart=30, rtol=1e-8, max_iters=5000)
+    x = x.cpu().numpy()
+    assert info["converged"]
+    assert np.linalg.norm(b - oracle.spmv(A, x)) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-6)
+    # the FP64 oracle's preconditioned solve reaches the same solution within the conditioning
+    z = oracle.ilu_apply(L, U, b)
+    zg = s.apply(dev(b)).cpu().numpy()
+    assert relmax(zg, z) <= 1e-5  # FP32 factor values: one apply within FP32-level error
+
+
+def test_cfg2_ilut_27pt_sweeps_1_and_16_rhs(hec):
+    m = 100
+    A = synth.stencil27_jitter(m, seed=0)
+    L, U = oracle.ilut(A, 10, 1e-3)
+    n = m ** 3
+    B = synth.uniform_vector(n, 0, nrhs=16)
+    for uplo, T in [(0, L), (1, U)]:
+        Td = [dev(a) for a in T]
+        lv = hec.sptrsv_analyze(Td[0], Td[1], uplo)
+        assert lv.nlev == oracle.levels(T, uplo)[1]
+        f = hec.sptrsv_lower if uplo == 0 else hec.sptrsv_upper
+        o = oracle.lower_solve if uplo == 0 else oracle.upper_solve
+        refs = {q: o(T, B[:, q]) for q in (0, 7, 15)}
+        # the width rule gives w = 10 here (most ILUT rows keep p = 10 entries); a narrower slab
+        # sends the rest of every long row to the CSR tail
+        for w in (-1, 6):
+            H = hec.hec_from_csr(*Td, levels=lv, ell_width=w, vdt="f64")
+            if w == 6:
+                assert H.info().tail_nnz > 2 * n
+            p = hec.sptrsv_plan_create(H, lv, 16)
+            x1 = f(p, dev(B[:, 0].copy())).cpu().numpy()
+            assert relmax(x1, refs[0]) <= 1e-12
+            X = f(p, dev(B)).cpu().numpy()
+            for q in (0, 7, 15):
+                assert relmax(X[:, q], refs[q]) <= 1e-12
+
+
+def test_cfg3_ras64_16_rhs(hec):
+    m = 128
+    A = synth.fv7_lognormal(m, sigma=2.0, seed=0)
+    part, ns = synth.box_partition(m, [25, 39, 25, 39])
+    assert ns == 64
+    Ro = oracle.ras_setup(A, part, ns)
+    assert int(Ro["ext_ptr"][-1]) == m ** 3 + 2 * 9 * m * m  # 2,392,064 extended rows
+    s = hec.RasSolver([dev(a) for a in A], dev(part), ns, vdt="f64", max_nrhs=16)
+    assert np.array_equal(s.ext_ptr.cpu().numpy(), Ro["ext_ptr"])
+    assert np.array_equal(s.ext2glob.cpu().numpy(), Ro["ext_idx"])
+    R = synth.uniform_vector(m ** 3, 9, nrhs=16)
+    Z = s.apply(dev(R)).cpu().numpy()
+    for q in (0, 5, 15):
+        assert relmax(Z[:, q], oracle.ras_apply(Ro, R[:, q])) <= 1e-11
+
+
+def test_cfg4_200cubed_levels_and_sweeps(hec):
+    m = 200
+    A = synth.fv7_lognormal(m, sigma=2.0, seed=0)
+    Ad = [dev(a) for a in A]
+    Lh, Uh = hec.ilu_factor(*Ad, k=0)
+    L = [t.cpu().numpy() for t in Lh.tensors()]
+    U = [t.cpu().numpy() for t in Uh.tensors()]
+    Lo, Uo = oracle.ilu0(A)
+    assert np.array_equal(L[1], Lo[1]) and relmax(L[2], Lo[2]) <= 1e-12
+    assert np.array_equal(U[1], Uo[1]) and relmax(U[2], Uo[2]) <= 1e-12
+    b = synth.uniform_vector(m ** 3, 2)
+    for uplo, T, Th in [(0, Lo, Lh), (1, Uo, Uh)]:
+        Td = Th.tensors()
+        lv = hec.sptrsv_analyze(Td[0], Td[1], uplo)
+        assert lv.nlev == 3 * m - 2  # 598
+        H = hec.hec_from_csr(*Td, levels=lv, vdt="f64")
+        p = hec.sptrsv_plan_create(H, lv, 1)
+        x = (hec.sptrsv_lower if uplo == 0 else hec.sptrsv_upper)(p, dev(b)).cpu().numpy()
+        assert relmax(x, (oracle.lower_solve if uplo == 0 else oracle.upper_solve)(T, b)) <= 1e-12
