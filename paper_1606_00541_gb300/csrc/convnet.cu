@@ -81,73 +81,184 @@ __device__ __forceinline__ void load_halo(const Geom& g, const __nv_bfloat16* __
     }
 }
 
+// ---- forward / data-gradient convolution ----------------------------------------------------
+// A block computes a 32 (x) x 4 (y) x 4 (z) output tile with 4 warps, warp w owning the z-plane w
+// of the tile (32 x 4 voxels = 2 m-tiles x 4 rows).  The 34 x 6 x 6 input halo and the weight
+// taps are staged in shared memory with cp.async.  Each 16-voxel A fragment of halo row (y', z')
+// shifted by dx is loaded once (ldmatrix) and multiplied into the (up to) three output rows that
+// read it through dy = 0, 1, 2, so every ldmatrix.x4 of A feeds 4 mma per n-tile.
+// Rows of 32 bytes (one voxel, or one output channel of a weight tap) are stored with their two
+// 16-byte halves swapped when bit 2 of the row index is set; any 8 consecutive rows then hit 8
+// distinct bank quads and ldmatrix runs without conflicts.
+constexpr int FX = 32, FY = 4, FZ = 4;                 // output tile of the forward kernel
+constexpr int GX = FX + 2, GY = FY + 2, GZ = FZ + 2;   // its input halo
+constexpr int kHaloBytes = GX * GY * GZ * 32;
+constexpr int kFwdSmem = kHaloBytes + NTAP * C * C * 2;
+
+__device__ __forceinline__ unsigned swz(unsigned row, unsigned half) { return row * 32u + ((half ^ ((row >> 2) & 1u)) << 4); }
+
+__device__ __forceinline__ void cp_async16(unsigned dst, const void* src, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], unsigned addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2(unsigned& r0, unsigned& r1, unsigned addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+
+// Modes of k_conv: PLAIN (16 -> NT*8 channels, 27 taps), MASKED (the input is multiplied by the
+// ReLU mask of the layer while it is staged: the data-gradient pass), EXPAND (the first layer:
+// only input channels 0 and 1 are read, and the halo entry at x holds channels 0-1 of the voxels
+// x-1, x, x+1 in its slots 0-5, so the three dx taps become one K = 16 product and the layer
+// takes 9 taps, with weights from k_weights_x).
+enum ConvMode { PLAIN = 0, MASKED = 1, EXPAND = 2 };
+
 // Y = conv(X, W) + bias, optional ReLU; Y0 (optional) receives channel 0 in FP32 times y0_scale.
-// W is [27][16 out][16 in] BF16.
-__global__ void __launch_bounds__(kConvThreads) k_conv_fwd(Geom g, const __nv_bfloat16* __restrict__ X,
-                                                           const __nv_bfloat16* __restrict__ mask,
-                                                           const __nv_bfloat16* __restrict__ W,
-                                                           const float* __restrict__ bias, int relu,
-                                                           __nv_bfloat16* __restrict__ Y, float* __restrict__ Y0,
-                                                           float y0_scale) {
-    __shared__ __align__(16) __nv_bfloat16 sx[HZ][HY][HX][C];
-    __shared__ __align__(16) __nv_bfloat16 sw[NTAP][C][C];
-    const int bx = blockIdx.x * TX, by = blockIdx.y * TY, bz = blockIdx.z;
-    for (int i = threadIdx.x; i < WSZ / 8; i += blockDim.x) ((uint4*)&sw[0][0][0])[i] = __ldg((const uint4*)W + i);
-    load_halo(g, X, mask, bx, by, bz, sx);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int gq = lane >> 2, t = lane & 3;
-    float acc[2][2][4];
+// W is [taps][16 out][16 in] BF16.  With NT = 1 only output channels 0-7 are computed and
+// channels 8-15 of Y are written as zeros (the last layer has one output channel).
+template <int MODE, int NT>
+__global__ void __launch_bounds__(kConvThreads, 4)
+    k_conv(Geom g, int ztiles, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ mask,
+           const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias, int relu,
+           __nv_bfloat16* __restrict__ Y, float* __restrict__ Y0, float y0_scale) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int ntap = MODE == EXPAND ? 9 : NTAP;
+    const unsigned sx = (unsigned)__cvta_generic_to_shared(smem);
+    const unsigned sw = sx + kHaloBytes;
+    const int x0 = blockIdx.x * FX, y0 = blockIdx.y * FY;
+    const int sample = blockIdx.z / ztiles, zl0 = (blockIdx.z - sample * ztiles) * FZ;
+    const long sbase = (long)sample * g.zs;
+    // weights: row = tap * 16 + out channel, two 16-byte halves of input channels
+    for (int i = threadIdx.x; i < ntap * C * 2; i += kConvThreads)
+        cp_async16(sw + swz(i >> 1, i & 1), W + (long)i * 8, 16);
+    if (MODE == EXPAND) {
+        for (int v = threadIdx.x; v < GX * GY * GZ; v += kConvThreads) {
+            const int hx = v % GX, hy = (v / GX) % GY, hz = v / (GX * GY);
+            const int y = y0 + hy - 1, z = zl0 + hz - 1;
+            unsigned e[4] = {0u, 0u, 0u, 0u};
+            if (y >= 0 && y < g.ny && z >= 0 && z < g.zs) {
+                const unsigned* row = (const unsigned*)(X + ((sbase + z) * g.ny + y) * (long)g.nx * C);
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+                for (int d = 0; d < 3; ++d) {
+                    const int x = x0 + hx - 2 + d;
+                    if (x >= 0 && x < g.nx) e[d] = __ldg(row + (long)x * (C / 2));
+                }
+            }
+            asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(sx + swz(v, 0)), "r"(e[0]), "r"(e[1]), "r"(e[2]),
+                         "r"(e[3]));
+            asm volatile("st.shared.v4.u32 [%0], {%1,%1,%1,%1};" ::"r"(sx + swz(v, 1)), "r"(0u));
+        }
+    } else {
+        for (int i = threadIdx.x; i < GX * GY * GZ * 2; i += kConvThreads) {
+            const int v = i >> 1, half = i & 1;
+            const int hx = v % GX, hy = (v / GX) % GY, hz = v / (GX * GY);
+            const int x = x0 + hx - 1, y = y0 + hy - 1, z = zl0 + hz - 1;
+            const bool in = x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.zs;
+            const long gi = in ? ((sbase + z) * g.ny + y) * g.nx + x : 0;
+            if (MODE == MASKED) {
+                uint4 val = make_uint4(0, 0, 0, 0);
+                if (in) val = apply_mask(__ldg((const uint4*)X + gi * 2 + half), __ldg((const uint4*)mask + gi * 2 + half));
+                asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(sx + swz(v, half)), "r"(val.x), "r"(val.y),
+                             "r"(val.z), "r"(val.w));
+            } else {
+                cp_async16(sx + swz(v, half), X + gi * C + half * 8, in ? 16 : 0);
+            }
+        }
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int zl = zl0 + w;
+    if (zl >= g.zs) return;  // no barrier follows
+    const int gq = lane >> 2, t = lane & 3;
+    // ldmatrix row addresses: lane l gives row (l & 7) of matrix (l >> 3)
+    const int lr = lane & 7, lm = lane >> 3;
+    const int a_off = lr + (lm & 1) * 8, a_half = lm >> 1;  // A: voxel offset, channel half
+    const int b_row = lr + (lm >> 1) * 8, b_half = lm & 1;  // B: output channel, input-channel half
+
+    float acc[FY][2][NT][4];
+#pragma unroll
+    for (int a = 0; a < FY; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-#pragma unroll 3
-    for (int tap = 0; tap < NTAP; ++tap) {
-        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-        unsigned bf[2][2];
+            for (int c = 0; c < NT; ++c)
 #pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-            bf[nt][0] = *(const unsigned*)&sw[tap][nt * 8 + gq][2 * t];
-            bf[nt][1] = *(const unsigned*)&sw[tap][nt * 8 + gq][2 * t + 8];
-        }
+                for (int d = 0; d < 4; ++d) acc[a][b][c][d] = 0.f;
+
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            const int hx = mt * 16 + gq + dx;
-            unsigned af[4];
-            af[0] = *(const unsigned*)&sx[dz][w + dy][hx][2 * t];
-            af[1] = *(const unsigned*)&sx[dz][w + dy][hx + 8][2 * t];
-            af[2] = *(const unsigned*)&sx[dz][w + dy][hx][2 * t + 8];
-            af[3] = *(const unsigned*)&sx[dz][w + dy][hx + 8][2 * t + 8];
-            mma_bf16(acc[mt][0], af, bf[0]);
-            mma_bf16(acc[mt][1], af, bf[1]);
+    for (int dz = 0; dz < 3; ++dz) {
+#pragma unroll
+        for (int dxi = 0; dxi < (MODE == EXPAND ? 1 : 3); ++dxi) {
+            const int dx = MODE == EXPAND ? 1 : dxi;
+            unsigned bf[3][NT][2];
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy) {
+                const int tap = MODE == EXPAND ? dz * 3 + dy : (dz * 3 + dy) * 3 + dx;
+                const unsigned row = tap * C + b_row;
+                if constexpr (NT == 2) {
+                    unsigned r[4];
+                    ldsm_x4(r, sw + swz(row, b_half));
+                    bf[dy][0][0] = r[0];
+                    bf[dy][0][1] = r[1];
+                    bf[dy][1][0] = r[2];
+                    bf[dy][1][1] = r[3];
+                } else {
+                    ldsm_x2(bf[dy][0][0], bf[dy][0][1], sw + swz(tap * C + lr, lm & 1));
+                }
+            }
+#pragma unroll
+            for (int yi = 0; yi < GY; ++yi) {
+                unsigned af[2][4];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    const unsigned v = ((w + dz) * GY + yi) * GX + mt * 16 + dx + a_off;
+                    ldsm_x4(af[mt], sx + swz(v, a_half));
+                }
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy) {
+                    const int ly = yi - dy;
+                    if (ly < 0 || ly >= FY) continue;
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                        for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[ly][mt][nt], af[mt], bf[dy][nt]);
+                }
+            }
         }
     }
-    const int y = by + w;
-    if (y >= g.ny) return;
+
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
+    for (int ly = 0; ly < FY; ++ly) {
+        const int y = y0 + ly;
+        if (y >= g.ny) break;
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int x = bx + mt * 16 + gq + half * 8;
-            if (x >= g.nx) continue;
-            const long vox = ((long)bz * g.ny + y) * g.nx + x;
+        for (int mt = 0; mt < 2; ++mt) {
 #pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-                const int co = nt * 8 + 2 * t;
-                float v0 = acc[mt][nt][half * 2 + 0], v1 = acc[mt][nt][half * 2 + 1];
-                if (bias) {
-                    v0 += bias[co];
-                    v1 += bias[co + 1];
+            for (int half = 0; half < 2; ++half) {
+                const int x = x0 + mt * 16 + gq + half * 8;
+                if (x >= g.nx) continue;
+                const long vox = ((sbase + zl) * g.ny + y) * g.nx + x;
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    const int co = nt * 8 + 2 * t;
+                    float v0 = acc[ly][mt][nt][half * 2 + 0], v1 = acc[ly][mt][nt][half * 2 + 1];
+                    if (bias) {
+                        v0 += bias[co];
+                        v1 += bias[co + 1];
+                    }
+                    if (relu) {
+                        v0 = fmaxf(v0, 0.f);
+                        v1 = fmaxf(v1, 0.f);
+                    }
+                    *(unsigned*)&Y[vox * C + co] = pack2(__float2bfloat16_rn(v0), __float2bfloat16_rn(v1));
+                    if (NT == 1) *(unsigned*)&Y[vox * C + co + 8] = 0u;
+                    if (Y0 && co == 0) Y0[vox] = v0 * y0_scale;
                 }
-                if (relu) {
-                    v0 = fmaxf(v0, 0.f);
-                    v1 = fmaxf(v1, 0.f);
-                }
-                *(unsigned*)&Y[vox * C + co] = pack2(__float2bfloat16_rn(v0), __float2bfloat16_rn(v1));
-                if (Y0 && co == 0) Y0[vox] = v0 * y0_scale;
             }
         }
     }
@@ -241,14 +352,18 @@ __global__ void k_reduce_partials(int nblk, const float* __restrict__ partial, f
 }
 
 // From FP32 master parameters P[tap][ci][co] (+ bias) to the BF16 forward layout Wf[tap][co][ci]
-// and the data-gradient layout Wd[26 - tap][ci][co] (flipped taps, channels transposed).
-__global__ void k_weights(const float* __restrict__ P, __nv_bfloat16* __restrict__ Wf, __nv_bfloat16* __restrict__ Wd) {
+// and the data-gradient layout Wd[26 - tap][ci][co] (flipped taps, channels transposed).  For the
+// first layer, Wx (when given) receives the x-expanded layout of its input channels 0 and 1:
+// Wx[dz * 3 + dy][co][2 dx + ci] (slots 6-15 stay zero).
+__global__ void k_weights(const float* __restrict__ P, __nv_bfloat16* __restrict__ Wf, __nv_bfloat16* __restrict__ Wd,
+                          __nv_bfloat16* __restrict__ Wx) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= WSZ) return;
     const int tap = j / (C * C), ci = (j / C) % C, co = j % C;
     const __nv_bfloat16 v = __float2bfloat16_rn(P[j]);
     Wf[(tap * C + co) * C + ci] = v;
     Wd[((NTAP - 1 - tap) * C + ci) * C + co] = v;
+    if (Wx && ci < 2) Wx[((tap / 3) * C + co) * C + 2 * (tap % 3) + ci] = v;
 }
 
 __global__ void k_adam(int n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -297,6 +412,7 @@ struct hec_net {
     float* V = nullptr;                // Adam second moment
     __nv_bfloat16* Wf = nullptr;       // [NL][WSZ] forward weights
     __nv_bfloat16* Wd = nullptr;       // [NL][WSZ] data-gradient weights
+    __nv_bfloat16* Wx = nullptr;       // [9][16][16] first layer, x-expanded input channels
     int step = 0;
     long cap = 0;                      // voxels the activation buffers hold
     __nv_bfloat16* act[hec::NL + 1] = {};  // act[0] = input, act[l] = output of layer l
@@ -312,7 +428,7 @@ namespace {
 
 void free_net(hec_net* N) {
     if (!N) return;
-    cudaFree(N->P); cudaFree(N->G); cudaFree(N->M); cudaFree(N->V); cudaFree(N->Wf); cudaFree(N->Wd);
+    cudaFree(N->P); cudaFree(N->G); cudaFree(N->M); cudaFree(N->V); cudaFree(N->Wf); cudaFree(N->Wd); cudaFree(N->Wx);
     for (auto& a : N->act) cudaFree(a);
     for (auto& a : N->dA) cudaFree(a);
     cudaFree(N->out); cudaFree(N->partial); cudaFree(N->lpart);
@@ -342,12 +458,14 @@ hec_status ensure(hec_net* N, long nvox, long nblk) {
 
 hec_status refresh_weights(hec_net* N, cudaStream_t s) {
     for (int l = 0; l < NL; ++l)
-        k_weights<<<(WSZ + 255) / 256, 256, 0, s>>>(N->P + (long)l * PSZ, N->Wf + (long)l * WSZ, N->Wd + (long)l * WSZ);
+        k_weights<<<(WSZ + 255) / 256, 256, 0, s>>>(N->P + (long)l * PSZ, N->Wf + (long)l * WSZ, N->Wd + (long)l * WSZ,
+                                                    l == 0 ? N->Wx : nullptr);
     count_launch(NL);
     HEC_CUDA(cudaGetLastError());
     return HEC_OK;
 }
 
+// grid of the weight-gradient kernel (one 32 x 4 x 1 tile per block)
 dim3 conv_grid(const Geom& g) { return dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, g.nz); }
 
 hec_status check_geom(const Geom& g) {
@@ -357,16 +475,32 @@ hec_status check_geom(const Geom& g) {
     return HEC_OK;
 }
 
+// one forward-type convolution (see k_conv)
+template <int MODE, int NT>
+hec_status conv(const Geom& g, const __nv_bfloat16* X, const __nv_bfloat16* mask, const __nv_bfloat16* W,
+                const float* bias, int relu, __nv_bfloat16* Y, float* Y0, float y0_scale, cudaStream_t s) {
+    static bool smem_set = false;
+    if (!smem_set) {
+        HEC_CUDA(cudaFuncSetAttribute(k_conv<MODE, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem));
+        smem_set = true;
+    }
+    const int zt = (g.zs + FZ - 1) / FZ;
+    const dim3 grid((g.nx + FX - 1) / FX, (g.ny + FY - 1) / FY, (g.nz / g.zs) * zt);
+    k_conv<MODE, NT><<<grid, kConvThreads, kFwdSmem, s>>>(g, zt, X, mask, W, bias, relu, Y, Y0, y0_scale);
+    count_launch();
+    return HEC_OK;
+}
+
 // forward through all layers from N->act[0]; the FP32 output (times scale) lands in N->out
 hec_status forward(hec_net* N, const Geom& g, float scale, cudaStream_t s) {
-    const dim3 grid = conv_grid(g);
-    for (int l = 0; l < NL; ++l) {
-        const bool last = l == NL - 1;
-        ProfScope ps_(s, PROF_VEC);
-        k_conv_fwd<<<grid, kConvThreads, 0, s>>>(g, N->act[l], nullptr, N->Wf + (long)l * WSZ, N->P + (long)l * PSZ + WSZ,
-                                                 last ? 0 : 1, N->act[l + 1], last ? N->out : nullptr, scale);
-    }
-    count_launch(NL);
+    ProfScope ps_(s, PROF_VEC);
+    const float* b[NL];
+    for (int l = 0; l < NL; ++l) b[l] = N->P + (long)l * PSZ + WSZ;
+    HEC_CHECK((conv<EXPAND, 2>(g, N->act[0], nullptr, N->Wx, b[0], 1, N->act[1], nullptr, 1.f, s)));
+    for (int l = 1; l < NL - 1; ++l)
+        HEC_CHECK((conv<PLAIN, 2>(g, N->act[l], nullptr, N->Wf + (long)l * WSZ, b[l], 1, N->act[l + 1], nullptr, 1.f, s)));
+    HEC_CHECK((conv<PLAIN, 1>(g, N->act[NL - 1], nullptr, N->Wf + (long)(NL - 1) * WSZ, b[NL - 1], 0, N->act[NL], N->out,
+                              scale, s)));
     HEC_CUDA(cudaGetLastError());
     return HEC_OK;
 }
@@ -382,9 +516,12 @@ hec_status backward(hec_net* N, const Geom& g, cudaStream_t s) {
         k_reduce_partials<<<(PSZ + 255) / 256, 256, 0, s>>>((int)nblk, N->partial, N->G + (long)l * PSZ);
         count_launch(2);
         if (l > 0) {
-            k_conv_fwd<<<grid, kConvThreads, 0, s>>>(g, N->dA[cur], mask, N->Wd + (long)l * WSZ, nullptr, 0,
-                                                     N->dA[cur ^ 1], nullptr, 1.f);
-            count_launch();
+            if (mask)
+                HEC_CHECK((conv<MASKED, 2>(g, N->dA[cur], mask, N->Wd + (long)l * WSZ, nullptr, 0, N->dA[cur ^ 1], nullptr,
+                                           1.f, s)));
+            else
+                HEC_CHECK((conv<PLAIN, 2>(g, N->dA[cur], nullptr, N->Wd + (long)l * WSZ, nullptr, 0, N->dA[cur ^ 1],
+                                          nullptr, 1.f, s)));
             cur ^= 1;
         }
     }
@@ -481,7 +618,8 @@ HEC_API hec_status net_create(const float* params, hec_net** out) {
     const size_t np = (size_t)NL * PSZ;
     hec_status st = HEC_OK;
     if ((st = dalloc(&N->P, np)) || (st = dalloc(&N->G, np)) || (st = dalloc(&N->M, np)) || (st = dalloc(&N->V, np)) ||
-        (st = dalloc(&N->Wf, (size_t)NL * WSZ)) || (st = dalloc(&N->Wd, (size_t)NL * WSZ)) || (st = dalloc(&N->lpart, 4096))) {
+        (st = dalloc(&N->Wf, (size_t)NL * WSZ)) || (st = dalloc(&N->Wd, (size_t)NL * WSZ)) ||
+        (st = dalloc(&N->Wx, (size_t)9 * C * C)) || (st = dalloc(&N->lpart, 4096))) {
         free_net(N);
         return st;
     }
@@ -489,6 +627,7 @@ HEC_API hec_status net_create(const float* params, hec_net** out) {
     cudaMemset(N->M, 0, sizeof(float) * np);
     cudaMemset(N->V, 0, sizeof(float) * np);
     cudaMemset(N->G, 0, sizeof(float) * np);
+    cudaMemset(N->Wx, 0, sizeof(__nv_bfloat16) * 9 * C * C);
     st = refresh_weights(N, 0);
     if (st == HEC_OK && cudaDeviceSynchronize() != cudaSuccess) st = cuda_error(cudaGetLastError(), "net_create");
     if (st) { free_net(N); return st; }

@@ -97,6 +97,27 @@ def train(net, samples, crop, epochs=4, batch=8, lr=1e-3, seed=0, log=None):
     return hist
 
 
+def forward_timing(m, reps=10, seed=0):
+    """Times the network's forward pass on an m^3 field (random input, seeded initial weights):
+    returns (ms per forward, TFLOP/s counting the 16 x 16 channel products of every layer)."""
+    net = hec.Net(init_params(seed))
+    n = m ** 3
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    x = torch.zeros(n, C, dtype=torch.bfloat16, device="cuda")
+    x[:, :2] = torch.randn(n, 2, device="cuda", generator=g).to(torch.bfloat16)
+    for _ in range(2):
+        net.forward(x, (m, m, m))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        net.forward(x, (m, m, m))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return ms, 4 * n * 27 * C * C * 2 / ms / 1e9
+
+
 def train_stage(lnk_full, m_full, crop=64, crops=125, rhs_per_crop=16, epochs=4, batch=8, lr=1e-3, seed=0,
                 log=None):
     """Generates the pairs and trains a network from scratch; returns (net, info)."""
@@ -111,3 +132,15 @@ def train_stage(lnk_full, m_full, crop=64, crops=125, rhs_per_crop=16, epochs=4,
     t2 = time.perf_counter()
     return net, dict(pairs=len(samples), crop=crop, data_s=t1 - t0, train_s=t2 - t1, loss_first=hist[0] if hist else None,
                      loss_last=float(np.mean(hist[-10:])) if hist else None, steps=len(hist))
+
+
+if __name__ == "__main__":
+    import argparse
+
+    ap = argparse.ArgumentParser(description="correction-network utilities")
+    ap.add_argument("command", choices=["forward"])
+    ap.add_argument("--size", type=int, default=128)
+    ap.add_argument("--reps", type=int, default=10)
+    a = ap.parse_args()
+    ms, tf = forward_timing(a.size, a.reps)
+    print("forward %d^3: %.3f ms, %.1f TFLOP/s" % (a.size, ms, tf))
