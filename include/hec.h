@@ -310,10 +310,18 @@ hec_status net_make_sample(int n, const double* r, const double* e, const double
 /* The stage used by fgmres_solve: with z1 = M^-1 v (the ILU sweep) and r1 = v - A z1,
  * c = sigma * Net([r1 / sigma, aux_scale * aux]) with sigma = RMS(r1), alpha = <r1, A c> /
  * <A c, A c>, and z = z1 + alpha c when alpha > 0 and ||r1 - alpha A c|| < rho ||r1||, else z = z1
- * (the plain ILU result: the fallback).  A: the FP64 general-mode matrix on an nx*ny*nz grid;
+ * (the plain ILU result: the fallback).  sigma comes from FP64 sums; alpha and the acceptance
+ * test from FP32 partial sums (they only scale the correction).  Inside fgmres_solve a stage on
+ * the solver's own A also returns A z = (v - r1) + alpha A c, which replaces the solver's product.
+ * A: the FP64 general-mode matrix on an nx*ny*nz grid;
  * aux: device FP64 [n] second input field (e.g. ln k), copied.  The net is borrowed. */
 hec_status stage_create(hec_net* net, const hec_matrix* A, int nx, int ny, int nz,
                         const double* aux, double aux_scale, double rho, hec_stage** out);
+/* One application of the stage outside the solver, as fgmres_solve applies it: v (device FP64
+ * [n]) is the vector to precondition, z (device FP64 [n]) holds z1 = M^-1 v on entry (e.g. from
+ * ilu_apply) and z1 or z1 + alpha c on return.  Asynchronous on `stream`; counts toward
+ * stage_stats. */
+hec_status stage_apply(const hec_stage* stage, const double* v, double* z, void* stream);
 /* Applications and accepted corrections since creation or the last reset. */
 hec_status stage_stats(const hec_stage* stage, int* applied, int* accepted, int reset);
 hec_status stage_destroy(hec_stage* stage);

@@ -113,17 +113,36 @@ __device__ __forceinline__ void ldsm_x2(unsigned& r0, unsigned& r1, unsigned add
 // ReLU mask of the layer while it is staged: the data-gradient pass), EXPAND (the first layer:
 // only input channels 0 and 1 are read, and the halo entry at x holds channels 0-1 of the voxels
 // x-1, x, x+1 in its slots 0-5, so the three dx taps become one K = 16 product and the layer
-// takes 9 taps, with weights from k_weights_x).
+// takes 9 taps, with weights from k_weights' Wx).
 enum ConvMode { PLAIN = 0, MASKED = 1, EXPAND = 2 };
 
-// Y = conv(X, W) + bias, optional ReLU; Y0 (optional) receives channel 0 in FP32 times y0_scale.
-// W is [taps][16 out][16 in] BF16.  With NT = 1 only output channels 0-7 are computed and
-// channels 8-15 of Y are written as zeros (the last layer has one output channel).
+// Input of k_conv: the 16-channel field X (ReLU mask for MASKED), or, for EXPAND with r given,
+// the two input channels straight from the solver's vectors: channel 0 = BF16(r / sigma)
+// (0 when sigma is not positive), channel 1 = aux.
+struct ConvIn {
+    const __nv_bfloat16* X;
+    const __nv_bfloat16* mask;
+    const double* r;
+    const double* sigma;
+    const __nv_bfloat16* aux;
+};
+// Outputs: Y (16-channel BF16, optional), Y0 = channel 0 in FP32 times y0_scale (optional),
+// Yd = channel 0 times *yd_scale in FP64 (optional; channel 0 is first rounded to FP32).
+struct ConvOut {
+    __nv_bfloat16* Y;
+    float* Y0;
+    float y0_scale;
+    double* Yd;
+    const double* yd_scale;
+};
+
+// Y = conv(X, W) + bias, optional ReLU.  W is [taps][16 out][16 in] BF16.  With NT = 1 only
+// output channels 0-7 are computed and channels 8-15 of Y are written as zeros (the last layer
+// has one output channel).
 template <int MODE, int NT>
 __global__ void __launch_bounds__(kConvThreads, 4)
-    k_conv(Geom g, int ztiles, const __nv_bfloat16* __restrict__ X, const __nv_bfloat16* __restrict__ mask,
-           const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias, int relu,
-           __nv_bfloat16* __restrict__ Y, float* __restrict__ Y0, float y0_scale) {
+    k_conv(Geom g, int ztiles, ConvIn in, const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias, int relu,
+           ConvOut out) {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int ntap = MODE == EXPAND ? 9 : NTAP;
     const unsigned sx = (unsigned)__cvta_generic_to_shared(smem);
@@ -131,24 +150,36 @@ __global__ void __launch_bounds__(kConvThreads, 4)
     const int x0 = blockIdx.x * FX, y0 = blockIdx.y * FY;
     const int sample = blockIdx.z / ztiles, zl0 = (blockIdx.z - sample * ztiles) * FZ;
     const long sbase = (long)sample * g.zs;
+    const __nv_bfloat16* __restrict__ X = in.X;
     // weights: row = tap * 16 + out channel, two 16-byte halves of input channels
     for (int i = threadIdx.x; i < ntap * C * 2; i += kConvThreads)
         cp_async16(sw + swz(i >> 1, i & 1), W + (long)i * 8, 16);
-    if (MODE == EXPAND) {
-        for (int v = threadIdx.x; v < GX * GY * GZ; v += kConvThreads) {
-            const int hx = v % GX, hy = (v / GX) % GY, hz = v / (GX * GY);
-            const int y = y0 + hy - 1, z = zl0 + hz - 1;
-            unsigned e[4] = {0u, 0u, 0u, 0u};
-            if (y >= 0 && y < g.ny && z >= 0 && z < g.zs) {
-                const unsigned* row = (const unsigned*)(X + ((sbase + z) * g.ny + y) * (long)g.nx * C);
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const int x = x0 + hx - 2 + d;
-                    if (x >= 0 && x < g.nx) e[d] = __ldg(row + (long)x * (C / 2));
-                }
+    if constexpr (MODE == EXPAND) {
+        // 1) channels 0-1 of the voxels x0 - 2 .. x0 + 33 of every halo row, packed in one word
+        constexpr int RX = GX + 2;
+        unsigned* raw = (unsigned*)(smem + kHaloBytes + 9 * C * C * 2);
+        double inv = 0.0;
+        if (in.r) inv = *in.sigma > 0.0 ? 1.0 / *in.sigma : 0.0;
+        for (int i = threadIdx.x; i < RX * GY * GZ; i += kConvThreads) {
+            const int rx = i % RX, hy = (i / RX) % GY, hz = i / (RX * GY);
+            const int x = x0 + rx - 2, y = y0 + hy - 1, z = zl0 + hz - 1;
+            unsigned word = 0u;
+            if (x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.zs) {
+                const long gi = ((sbase + z) * g.ny + y) * g.nx + x;
+                if (in.r)
+                    word = pack2(__float2bfloat16_rn((float)(__ldg(in.r + gi) * inv)), in.aux[gi]);
+                else
+                    word = __ldg((const unsigned*)(X + gi * C));
             }
-            asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(sx + swz(v, 0)), "r"(e[0]), "r"(e[1]), "r"(e[2]),
-                         "r"(e[3]));
+            raw[i] = word;
+        }
+        __syncthreads();
+        // 2) the expanded halo entries
+        for (int v = threadIdx.x; v < GX * GY * GZ; v += kConvThreads) {
+            const int hx = v % GX, hyz = v / GX;
+            const unsigned* rr = raw + hyz * RX + hx;
+            asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(sx + swz(v, 0)), "r"(rr[0]), "r"(rr[1]), "r"(rr[2]),
+                         "r"(0u));
             asm volatile("st.shared.v4.u32 [%0], {%1,%1,%1,%1};" ::"r"(sx + swz(v, 1)), "r"(0u));
         }
     } else {
@@ -156,15 +187,15 @@ __global__ void __launch_bounds__(kConvThreads, 4)
             const int v = i >> 1, half = i & 1;
             const int hx = v % GX, hy = (v / GX) % GY, hz = v / (GX * GY);
             const int x = x0 + hx - 1, y = y0 + hy - 1, z = zl0 + hz - 1;
-            const bool in = x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.zs;
-            const long gi = in ? ((sbase + z) * g.ny + y) * g.nx + x : 0;
-            if (MODE == MASKED) {
+            const bool inb = x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.zs;
+            const long gi = inb ? ((sbase + z) * g.ny + y) * g.nx + x : 0;
+            if constexpr (MODE == MASKED) {
                 uint4 val = make_uint4(0, 0, 0, 0);
-                if (in) val = apply_mask(__ldg((const uint4*)X + gi * 2 + half), __ldg((const uint4*)mask + gi * 2 + half));
+                if (inb) val = apply_mask(__ldg((const uint4*)X + gi * 2 + half), __ldg((const uint4*)in.mask + gi * 2 + half));
                 asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(sx + swz(v, half)), "r"(val.x), "r"(val.y),
                              "r"(val.z), "r"(val.w));
             } else {
-                cp_async16(sx + swz(v, half), X + gi * C + half * 8, in ? 16 : 0);
+                cp_async16(sx + swz(v, half), X + gi * C + half * 8, inb ? 16 : 0);
             }
         }
     }
@@ -255,9 +286,14 @@ __global__ void __launch_bounds__(kConvThreads, 4)
                         v0 = fmaxf(v0, 0.f);
                         v1 = fmaxf(v1, 0.f);
                     }
-                    *(unsigned*)&Y[vox * C + co] = pack2(__float2bfloat16_rn(v0), __float2bfloat16_rn(v1));
-                    if (NT == 1) *(unsigned*)&Y[vox * C + co + 8] = 0u;
-                    if (Y0 && co == 0) Y0[vox] = v0 * y0_scale;
+                    if (out.Y) {
+                        *(unsigned*)&out.Y[vox * C + co] = pack2(__float2bfloat16_rn(v0), __float2bfloat16_rn(v1));
+                        if (NT == 1) *(unsigned*)&out.Y[vox * C + co + 8] = 0u;
+                    }
+                    if (co == 0) {
+                        if (out.Y0) out.Y0[vox] = v0 * out.y0_scale;
+                        if (out.Yd) out.Yd[vox] = *out.yd_scale * (double)(v0 * out.y0_scale);
+                    }
                 }
             }
         }
@@ -477,8 +513,8 @@ hec_status check_geom(const Geom& g) {
 
 // one forward-type convolution (see k_conv)
 template <int MODE, int NT>
-hec_status conv(const Geom& g, const __nv_bfloat16* X, const __nv_bfloat16* mask, const __nv_bfloat16* W,
-                const float* bias, int relu, __nv_bfloat16* Y, float* Y0, float y0_scale, cudaStream_t s) {
+hec_status conv(const Geom& g, const ConvIn& in, const __nv_bfloat16* W, const float* bias, int relu, const ConvOut& out,
+                cudaStream_t s) {
     static bool smem_set = false;
     if (!smem_set) {
         HEC_CUDA(cudaFuncSetAttribute(k_conv<MODE, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem));
@@ -486,21 +522,28 @@ hec_status conv(const Geom& g, const __nv_bfloat16* X, const __nv_bfloat16* mask
     }
     const int zt = (g.zs + FZ - 1) / FZ;
     const dim3 grid((g.nx + FX - 1) / FX, (g.ny + FY - 1) / FY, (g.nz / g.zs) * zt);
-    k_conv<MODE, NT><<<grid, kConvThreads, kFwdSmem, s>>>(g, zt, X, mask, W, bias, relu, Y, Y0, y0_scale);
+    k_conv<MODE, NT><<<grid, kConvThreads, kFwdSmem, s>>>(g, zt, in, W, bias, relu, out);
     count_launch();
     return HEC_OK;
 }
 
-// forward through all layers from N->act[0]; the FP32 output (times scale) lands in N->out
-hec_status forward(hec_net* N, const Geom& g, float scale, cudaStream_t s) {
+// forward through all layers from `in` (N->act[0], or the solver's vectors); `last` receives
+// the last layer's output
+hec_status forward(hec_net* N, const Geom& g, const ConvIn& in, const ConvOut& last, cudaStream_t s) {
     ProfScope ps_(s, PROF_VEC);
     const float* b[NL];
     for (int l = 0; l < NL; ++l) b[l] = N->P + (long)l * PSZ + WSZ;
-    HEC_CHECK((conv<EXPAND, 2>(g, N->act[0], nullptr, N->Wx, b[0], 1, N->act[1], nullptr, 1.f, s)));
-    for (int l = 1; l < NL - 1; ++l)
-        HEC_CHECK((conv<PLAIN, 2>(g, N->act[l], nullptr, N->Wf + (long)l * WSZ, b[l], 1, N->act[l + 1], nullptr, 1.f, s)));
-    HEC_CHECK((conv<PLAIN, 1>(g, N->act[NL - 1], nullptr, N->Wf + (long)(NL - 1) * WSZ, b[NL - 1], 0, N->act[NL], N->out,
-                              scale, s)));
+    const ConvOut none{nullptr, nullptr, 1.f, nullptr, nullptr};
+    ConvOut o = none;
+    o.Y = N->act[1];
+    HEC_CHECK((conv<EXPAND, 2>(g, in, N->Wx, b[0], 1, o, s)));
+    for (int l = 1; l < NL - 1; ++l) {
+        o.Y = N->act[l + 1];
+        HEC_CHECK((conv<PLAIN, 2>(g, ConvIn{N->act[l], nullptr, nullptr, nullptr, nullptr}, N->Wf + (long)l * WSZ, b[l], 1,
+                                  o, s)));
+    }
+    HEC_CHECK((conv<PLAIN, 1>(g, ConvIn{N->act[NL - 1], nullptr, nullptr, nullptr, nullptr},
+                              N->Wf + (long)(NL - 1) * WSZ, b[NL - 1], 0, last, s)));
     HEC_CUDA(cudaGetLastError());
     return HEC_OK;
 }
@@ -516,12 +559,12 @@ hec_status backward(hec_net* N, const Geom& g, cudaStream_t s) {
         k_reduce_partials<<<(PSZ + 255) / 256, 256, 0, s>>>((int)nblk, N->partial, N->G + (long)l * PSZ);
         count_launch(2);
         if (l > 0) {
+            const ConvIn din{N->dA[cur], mask, nullptr, nullptr, nullptr};
+            const ConvOut dout{N->dA[cur ^ 1], nullptr, 1.f, nullptr, nullptr};
             if (mask)
-                HEC_CHECK((conv<MASKED, 2>(g, N->dA[cur], mask, N->Wd + (long)l * WSZ, nullptr, 0, N->dA[cur ^ 1], nullptr,
-                                           1.f, s)));
+                HEC_CHECK((conv<MASKED, 2>(g, din, N->Wd + (long)l * WSZ, nullptr, 0, dout, s)));
             else
-                HEC_CHECK((conv<PLAIN, 2>(g, N->dA[cur], nullptr, N->Wd + (long)l * WSZ, nullptr, 0, N->dA[cur ^ 1],
-                                          nullptr, 1.f, s)));
+                HEC_CHECK((conv<PLAIN, 2>(g, din, N->Wd + (long)l * WSZ, nullptr, 0, dout, s)));
             cur ^= 1;
         }
     }
@@ -529,35 +572,19 @@ hec_status backward(hec_net* N, const Geom& g, cudaStream_t s) {
     return HEC_OK;
 }
 
-__global__ void k_pack_input(long nvox, const double* __restrict__ r, const double* __restrict__ sigma,
-                             const __nv_bfloat16* __restrict__ aux, __nv_bfloat16* __restrict__ X) {
-    const double inv = *sigma > 0.0 ? 1.0 / *sigma : 0.0;
-    for (long v = (long)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (long)gridDim.x * blockDim.x) {
-        uint4 z0 = make_uint4(0, 0, 0, 0), z1 = z0;
-        z0.x = pack2(__float2bfloat16_rn((float)(r[v] * inv)), aux[v]);
-        ((uint4*)X)[v * 2] = z0;
-        ((uint4*)X)[v * 2 + 1] = z1;
-    }
-}
-
 }  // namespace
 
-// used by the learned FGMRES stage (krylov.cu)
+// used by the learned FGMRES stage (krylov.cu): c = sigma * Net([r / sigma, aux]) on an
+// nx x ny x nz grid, the input channels read straight from r and aux, c written in FP64
 hec_status net_apply_field(hec_net* N, int nx, int ny, int nz, const double* r, const double* sigma,
-                           const __nv_bfloat16* aux, cudaStream_t s) {
+                           const __nv_bfloat16* aux, double* c, cudaStream_t s) {
     Geom g{nx, ny, nz, nz};
     HEC_CHECK(check_geom(g));
     const long nvox = (long)nx * ny * nz;
     const dim3 grid = conv_grid(g);
     HEC_CHECK(ensure(N, nvox, (long)grid.x * grid.y * grid.z));
-    {
-        ProfScope ps_(s, PROF_VEC);
-        k_pack_input<<<(int)std::min<long>((nvox + 255) / 256, 65536), 256, 0, s>>>(nvox, r, sigma, aux, N->act[0]);
-    }
-    count_launch();
-    return forward(N, g, 1.f, s);
+    return forward(N, g, ConvIn{nullptr, nullptr, r, sigma, aux}, ConvOut{nullptr, nullptr, 1.f, c, sigma}, s);
 }
-const float* net_output(const hec_net* N) { return N->out; }
 
 }  // namespace hec
 
@@ -667,7 +694,8 @@ HEC_API hec_status net_forward(hec_net* N, int nx, int ny, int nz, int zs, const
     const dim3 grid = conv_grid(g);
     HEC_CHECK(ensure(N, nvox, (long)grid.x * grid.y * grid.z));
     HEC_CUDA(cudaMemcpyAsync(N->act[0], x_in, sizeof(__nv_bfloat16) * C * nvox, cudaMemcpyDeviceToDevice, s));
-    HEC_CHECK(forward(N, g, 1.f, s));
+    HEC_CHECK(forward(N, g, ConvIn{N->act[0], nullptr, nullptr, nullptr, nullptr},
+                      ConvOut{N->act[NL], N->out, 1.f, nullptr, nullptr}, s));
     if (acts_out)
         for (int l = 1; l <= NL; ++l)
             HEC_CUDA(cudaMemcpyAsync((__nv_bfloat16*)acts_out + (long)(l - 1) * nvox * C, N->act[l],
@@ -687,7 +715,8 @@ HEC_API hec_status net_train_step(hec_net* N, int nx, int ny, int nz, int zs, co
     const dim3 grid = conv_grid(g);
     HEC_CHECK(ensure(N, nvox, (long)grid.x * grid.y * grid.z));
     HEC_CUDA(cudaMemcpyAsync(N->act[0], x_in, sizeof(__nv_bfloat16) * C * nvox, cudaMemcpyDeviceToDevice, s));
-    HEC_CHECK(forward(N, g, 1.f, s));
+    HEC_CHECK(forward(N, g, ConvIn{N->act[0], nullptr, nullptr, nullptr, nullptr},
+                      ConvOut{N->act[NL], N->out, 1.f, nullptr, nullptr}, s));
     const int lb = 1024;
     k_mse<<<lb, 256, 0, s>>>(nvox, N->out, target, 1.f / (float)nvox, N->dA[0], N->lpart);
     count_launch();

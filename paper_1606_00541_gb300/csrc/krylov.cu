@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include <cooperative_groups.h>
@@ -33,7 +34,11 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kDotGroup = 8;  // dot products per block row of the multi-dot
 
-template <int KP>
+// y = alpha A x + beta y for K right-hand sides (x, y row-major with leading dimensions ldx,
+// ldy).  Each thread takes RPT rows (strided by the block's row count, so loads stay coalesced)
+// for one right-hand side; the rows' chains of FMAs are independent, which keeps more loads and
+// FP64 operations in flight.  Each row sums its ELL slots, then its tail, in order.
+template <int KP, int RPT>
 __global__ void __launch_bounds__(kThreads) k_spmv(int n, int ld, int w, const int* __restrict__ ell_col,
                                                    const double* __restrict__ ell_val, const int* __restrict__ tptr,
                                                    const int* __restrict__ tcol, const double* __restrict__ tval,
@@ -41,19 +46,40 @@ __global__ void __launch_bounds__(kThreads) k_spmv(int n, int ld, int w, const i
                                                    double beta, double* __restrict__ y, int ldy) {
     constexpr int RPB = kThreads / KP;
     const int q = threadIdx.x % KP;
-    const int r = blockIdx.x * RPB + threadIdx.x / KP;
-    if (r >= n || q >= K) return;
-    double acc = 0.0;
-    for (int k = 0; k < w; ++k) {
-        const long s = (long)k * ld + r;
-        const int c = __ldg(ell_col + s);
-        if (c < 0) break;
-        acc = fma(__ldg(ell_val + s), __ldg(x + (long)c * ldx + q), acc);
+    const int rb = blockIdx.x * RPB * RPT + threadIdx.x / KP;
+    if (q >= K || rb >= n) return;
+    double acc[RPT];
+    int row[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        acc[i] = 0.0;
+        row[i] = rb + i * RPB < n ? rb + i * RPB : -1;
     }
-    const int t1 = __ldg(tptr + r + 1);
-    for (int t = __ldg(tptr + r); t < t1; ++t) acc = fma(__ldg(tval + t), __ldg(x + (long)__ldg(tcol + t) * ldx + q), acc);
-    double* yp = y + (long)r * ldy + q;
-    *yp = beta == 0.0 ? alpha * acc : fma(beta, *yp, alpha * acc);
+    // padding (col -1) only ends a row; predicating it instead of leaving the loop lets the
+    // loads of all slots issue together
+#pragma unroll 4
+    for (int k = 0; k < w; ++k) {
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+            if (row[i] < 0) continue;
+            const long s = (long)k * ld + row[i];
+            const int c = __ldg(ell_col + s);
+            if (c >= 0) acc[i] = fma(__ldg(ell_val + s), __ldg(x + (long)c * ldx + q), acc[i]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        if (row[i] < 0) continue;
+        const int t1 = __ldg(tptr + row[i] + 1);
+        for (int t = __ldg(tptr + row[i]); t < t1; ++t)
+            acc[i] = fma(__ldg(tval + t), __ldg(x + (long)__ldg(tcol + t) * ldx + q), acc[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        if (row[i] < 0) continue;
+        double* yp = y + (long)row[i] * ldy + q;
+        *yp = beta == 0.0 ? (alpha == 1.0 ? acc[i] : alpha * acc[i]) : fma(beta, *yp, alpha * acc[i]);
+    }
 }
 
 // dst (dense n x K) = src (n x K with leading dimension lds)
@@ -249,21 +275,38 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_mgs(int n, int K, int j, i
         }
         __syncthreads();
     };
-    for (int a = 0; a <= j; ++a) {
-        const double* va = V + (long)a * vstride;
+    // h_0 = <v_0, w>; then one pass per projection a: w -= h_a v_a, and in the same pass the next
+    // inner product <v_{a+1}, w> (or <w, w> after the last), taken on the updated entries; the
+    // per-entry order of operations is modified Gram-Schmidt's
+    {
         double acc = 0.0;
         if (qa)
-            for (long r = r0; r < n; r += rs) acc = fma(va[r * K + q], w[r * K + q], acc);
-        reduce_all(acc, a & 1);
+            for (long r = r0; r < n; r += rs) acc = fma(V[r * K + q], w[r * K + q], acc);
+        reduce_all(acc, 0);
+    }
+    for (int a = 0; a <= j; ++a) {
+        const double* va = V + (long)a * vstride;
         const double h = hsh[q];
         if (blockIdx.x == 0 && threadIdx.x < K) st.h1[a * K + threadIdx.x] = hsh[threadIdx.x];
-        if (qa)
-            for (long r = r0; r < n; r += rs) w[r * K + q] = fma(-h, va[r * K + q], w[r * K + q]);
+        double acc = 0.0;
+        if (qa) {
+            if (a < j) {
+                const double* vn = va + vstride;
+                for (long r = r0; r < n; r += rs) {
+                    const double wr = fma(-h, va[r * K + q], w[r * K + q]);
+                    w[r * K + q] = wr;
+                    acc = fma(vn[r * K + q], wr, acc);
+                }
+            } else {
+                for (long r = r0; r < n; r += rs) {
+                    const double wr = fma(-h, va[r * K + q], w[r * K + q]);
+                    w[r * K + q] = wr;
+                    acc = fma(wr, wr, acc);
+                }
+            }
+        }
+        reduce_all(acc, (a + 1) & 1);
     }
-    double acc = 0.0;
-    if (qa)
-        for (long r = r0; r < n; r += rs) acc = fma(w[r * K + q], w[r * K + q], acc);
-    reduce_all(acc, (j + 1) & 1);
     if (blockIdx.x == 0) {
         if (threadIdx.x == 0) any = 0;
         __syncthreads();
@@ -374,10 +417,11 @@ hec_status spmv_impl(const hec_matrix* A, int K, double alpha, const double* x, 
     if (A->n == 0) return HEC_OK;
     auto go = [&](auto kp) -> hec_status {
         constexpr int KP = decltype(kp)::value;
-        int blocks = (int)(((long)A->n * KP + kThreads - 1) / kThreads);
+        constexpr int RPT = KP == 1 ? 2 : 1;
+        int blocks = (int)(((long)A->n * KP + (long)kThreads * RPT - 1) / ((long)kThreads * RPT));
         {
             ProfScope ps_(s, PROF_SPMV);
-            k_spmv<KP><<<blocks, kThreads, 0, s>>>(A->n, A->ld, A->w, A->ell_col, (const double*)A->ell_val, A->tptr,
+            k_spmv<KP, RPT><<<blocks, kThreads, 0, s>>>(A->n, A->ld, A->w, A->ell_col, (const double*)A->ell_val, A->tptr,
                                                    A->tcol, (const double*)A->tval, K, alpha, x, ldx, beta, y, ldy);
         }
         HEC_LAUNCHED();
@@ -392,42 +436,132 @@ hec_status spmv_impl(const hec_matrix* A, int K, double alpha, const double* x, 
 
 // ---- learned correction stage --------------------------------------------------------------
 hec_status net_apply_field(hec_net* N, int nx, int ny, int nz, const double* r, const double* sigma,
-                           const __nv_bfloat16* aux, cudaStream_t s);
-const float* net_output(const hec_net* N);
+                           const __nv_bfloat16* aux, double* c, cudaStream_t s);
 
 namespace {
 __global__ void k_f64_to_bf16_scaled(long n, const double* __restrict__ a, double scale, __nv_bfloat16* __restrict__ o) {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
         o[i] = __float2bfloat16_rn((float)(a[i] * scale));
 }
-// sigma = sqrt(sum r^2 / n)
-__global__ void k_sigma(double* scal, long n) {
-    if (threadIdx.x == 0) scal[0] = sqrt(fmax(scal[1], 0.0) / (double)n);
+constexpr int kStageRpt = 2;  // rows per thread of the stage's matrix products
+
+// The stage's matrix products on one right-hand side: y = b - A x (SUB) or y = A x, plus this
+// block's partial sums of y.y and y.u (u may be NULL) in part[block][0..1].  The rows sum as in
+// k_spmv.  With SUB the sums (||r1||^2, hence sigma) are FP64; otherwise they only feed the step
+// length alpha and its 1 % acceptance test, so they are taken in FP32, which leaves the scarce
+// FP64 pipe to the product itself.
+template <bool SUB>
+__global__ void __launch_bounds__(kThreads, 6) k_spmv_dots(int n, int ld, int w, const int* __restrict__ ell_col,
+                                                        const double* __restrict__ ell_val, const int* __restrict__ tptr,
+                                                        const int* __restrict__ tcol, const double* __restrict__ tval,
+                                                        const double* __restrict__ x, const double* __restrict__ b,
+                                                        double* __restrict__ y, const double* __restrict__ u,
+                                                        double* __restrict__ part) {
+    using T = typename std::conditional<SUB, double, float>::type;
+    __shared__ T red[kThreads / 32][2];
+    const int rb = blockIdx.x * kThreads * kStageRpt + threadIdx.x;
+    double acc[kStageRpt];
+    int row[kStageRpt];
+#pragma unroll
+    for (int i = 0; i < kStageRpt; ++i) {
+        acc[i] = 0.0;
+        row[i] = rb + i * kThreads < n ? rb + i * kThreads : -1;
+    }
+#pragma unroll 4
+    for (int k = 0; k < w; ++k) {
+#pragma unroll
+        for (int i = 0; i < kStageRpt; ++i) {
+            if (row[i] < 0) continue;
+            const long s = (long)k * ld + row[i];
+            const int c = __ldg(ell_col + s);
+            if (c >= 0) acc[i] = fma(__ldg(ell_val + s), __ldg(x + c), acc[i]);
+        }
+    }
+    T syy = 0, syu = 0;
+#pragma unroll
+    for (int i = 0; i < kStageRpt; ++i) {
+        if (row[i] < 0) continue;
+        const int t1 = __ldg(tptr + row[i] + 1);
+        for (int t = __ldg(tptr + row[i]); t < t1; ++t) acc[i] = fma(__ldg(tval + t), __ldg(x + __ldg(tcol + t)), acc[i]);
+        const double yi = SUB ? b[row[i]] - acc[i] : acc[i];
+        y[row[i]] = yi;
+        const T yf = (T)yi;
+        syy = fma(yf, yf, syy);
+        if (u) syu = fma(yf, (T)u[row[i]], syu);
+    }
+    for (int o = 16; o; o >>= 1) {
+        syy += __shfl_xor_sync(0xffffffffu, syy, o);
+        syu += __shfl_xor_sync(0xffffffffu, syu, o);
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[wp][0] = syy;
+        red[wp][1] = syu;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double s = 0.0;
+        for (int i = 0; i < kThreads / 32; ++i) s += (double)red[i][threadIdx.x];
+        part[2 * blockIdx.x + threadIdx.x] = s;
+    }
 }
-__global__ void k_scale_out(long n, const float* __restrict__ out, const double* __restrict__ scal, double* __restrict__ c) {
-    const double s = scal[0];
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        c[i] = s * (double)out[i];
-}
-// alpha = <r1, Ac> / <Ac, Ac>; accepted when alpha > 0 and ||r1 - alpha Ac||^2 < rho^2 ||r1||^2
-__global__ void k_stage_decide(double* scal, double rho, long n, int* counters) {
+
+// One block: the sums of the nblk partial pairs in a fixed order.  stage 0: scal[1] = ||r1||^2,
+// scal[0] = sigma = sqrt(||r1||^2 / n).  stage 1: scal[3] = <Ac, Ac>, scal[2] = <r1, Ac>, then
+// the decision: alpha = <r1, Ac> / <Ac, Ac> is kept in scal[4] when alpha > 0 and
+// ||r1 - alpha Ac||^2 = ||r1||^2 - alpha <r1, Ac> < rho^2 ||r1||^2, else scal[4] = 0 (fallback).
+constexpr int kReduceThreads = 1024;
+__global__ void __launch_bounds__(kReduceThreads) k_stage_reduce(int nblk, const double* __restrict__ part, int stage,
+                                                                 long n, double rho, double* scal, int* counters) {
+    __shared__ double red[kReduceThreads / 32][2];
+    double s0 = 0.0, s1 = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += kReduceThreads) {
+        s0 += part[2 * b];
+        s1 += part[2 * b + 1];
+    }
+    for (int o = 16; o; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5][0] = s0;
+        red[threadIdx.x >> 5][1] = s1;
+    }
+    __syncthreads();
     if (threadIdx.x != 0) return;
-    const double rac = scal[2], acac = scal[3], rr = scal[1];
+    double t0 = 0.0, t1 = 0.0;
+    for (int i = 0; i < kReduceThreads / 32; ++i) {
+        t0 += red[i][0];
+        t1 += red[i][1];
+    }
+    if (stage == 0) {
+        scal[1] = t0;
+        scal[0] = sqrt(fmax(t0, 0.0) / (double)n);
+        return;
+    }
+    scal[3] = t0;
+    scal[2] = t1;
+    const double rr = scal[1];
     double coef = 0.0;
-    if (acac > 0.0) {
-        const double alpha = rac / acac;
-        const double left = rr - alpha * rac;  // ||r1 - alpha Ac||^2 at the optimal alpha
+    if (t0 > 0.0) {
+        const double alpha = t1 / t0;
+        const double left = rr - alpha * t1;  // ||r1 - alpha Ac||^2 at the optimal alpha
         if (alpha > 0.0 && left < rho * rho * rr) coef = alpha;
     }
     scal[4] = coef;
     counters[0] += 1;
     if (coef != 0.0) counters[1] += 1;
 }
-__global__ void k_axpy_dev(long n, const double* __restrict__ coef, const double* __restrict__ c, double* __restrict__ z) {
-    const double a = *coef;
-    if (a == 0.0) return;
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        z[i] = fma(a, c[i], z[i]);
+
+// z = z1 + coef c; and, when Az is given, Az = A z = (v - r1) + coef Ac
+__global__ void k_stage_finish(long n, const double* __restrict__ scal, const double* __restrict__ c,
+                               const double* __restrict__ v, const double* __restrict__ r1,
+                               const double* __restrict__ Ac, double* __restrict__ z, double* __restrict__ Az) {
+    const double a = scal[4];
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        if (a != 0.0) z[i] = fma(a, c[i], z[i]);
+        if (Az) Az[i] = a != 0.0 ? fma(a, Ac[i], v[i] - r1[i]) : v[i] - r1[i];
+    }
 }
 }  // namespace
 
@@ -444,29 +578,42 @@ struct hec_stage {
     double* work = nullptr;        // [3n]: r1 | Ac | c
     double* scal = nullptr;        // sigma, ||r1||^2, <r1,Ac>, <Ac,Ac>, coef
     int* counters = nullptr;       // applications, accepted corrections
-    hec::Dots* dots = nullptr;
+    double* part = nullptr;        // per-block partial sums of the matrix products
 };
 
 namespace hec {
-hec_status stage_apply(const hec_stage* S, const double* v, double* z, cudaStream_t s) {
-    const int n = S->A->n;
+int stage_blocks(long n) { return (int)((n + (long)kThreads * kStageRpt - 1) / ((long)kThreads * kStageRpt)); }
+
+// One application; z holds z1 on entry.  When Az is given it receives A z (the product FGMRES
+// needs next), assembled from the two products the stage computes anyway.
+hec_status stage_run(const hec_stage* S, const double* v, double* z, double* Az, cudaStream_t s) {
+    const hec_matrix* A = S->A;
+    const int n = A->n;
     double* r1 = S->work;
     double* Ac = S->work + n;
     double* c = S->work + 2 * (long)n;
-    const int gb = grid_for(n);
-    HEC_CUDA(cudaMemcpyAsync(r1, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    HEC_CHECK(spmv_impl(S->A, 1, -1.0, z, 1, 1.0, r1, 1, s));                     // r1 = v - A z1
-    HEC_CHECK(S->dots->run(n, 1, r1, n, 0, 1, r1, S->scal + 1, nullptr, s));      // ||r1||^2
-    k_sigma<<<1, 32, 0, s>>>(S->scal, n);
-    count_launch();
-    HEC_CHECK(net_apply_field(S->net, S->nx, S->ny, S->nz, r1, S->scal, S->aux, s));
-    k_scale_out<<<gb, kThreads, 0, s>>>(n, net_output(S->net), S->scal, c);       // c = sigma * Net
-    count_launch();
-    HEC_CHECK(spmv_impl(S->A, 1, 1.0, c, 1, 0.0, Ac, 1, s));                      // Ac
-    HEC_CHECK(S->dots->run(n, 1, S->work, n, 2, 0, Ac, S->scal + 2, nullptr, s));  // <r1,Ac>, <Ac,Ac>
-    k_stage_decide<<<1, 32, 0, s>>>(S->scal, S->rho, n, S->counters);
-    k_axpy_dev<<<gb, kThreads, 0, s>>>(n, S->scal + 4, c, z);
+    const int nb = stage_blocks(n);
+    const double* ev = (const double*)A->ell_val;
+    const double* tv = (const double*)A->tval;
+    {
+        ProfScope ps_(s, PROF_SPMV);  // r1 = v - A z1, ||r1||^2, sigma
+        k_spmv_dots<true><<<nb, kThreads, 0, s>>>(n, A->ld, A->w, A->ell_col, ev, A->tptr, A->tcol, tv, z, v, r1, nullptr,
+                                                  S->part);
+        k_stage_reduce<<<1, kReduceThreads, 0, s>>>(nb, S->part, 0, n, S->rho, S->scal, S->counters);
+    }
     count_launch(2);
+    HEC_CHECK(net_apply_field(S->net, S->nx, S->ny, S->nz, r1, S->scal, S->aux, c, s));  // c = sigma * Net
+    {
+        ProfScope ps_(s, PROF_SPMV);  // Ac, <Ac, Ac>, <r1, Ac>, alpha and the decision
+        k_spmv_dots<false><<<nb, kThreads, 0, s>>>(n, A->ld, A->w, A->ell_col, ev, A->tptr, A->tcol, tv, c, nullptr, Ac,
+                                                   r1, S->part);
+        k_stage_reduce<<<1, kReduceThreads, 0, s>>>(nb, S->part, 1, n, S->rho, S->scal, S->counters);
+    }
+    {
+        ProfScope ps_(s, PROF_VEC);
+        k_stage_finish<<<grid_for(n), kThreads, 0, s>>>(n, S->scal, c, v, r1, Ac, z, Az);
+    }
+    count_launch(3);
     HEC_CUDA(cudaGetLastError());
     return HEC_OK;
 }
@@ -487,23 +634,29 @@ HEC_API hec_status stage_create(hec_net* net, const hec_matrix* A, int nx, int n
     S->ny = ny;
     S->nz = nz;
     S->rho = rho;
-    S->dots = new Dots();
     const long n = A->n;
     hec_status st = HEC_OK;
     auto fail = [&](hec_status e) {
-        cudaFree(S->aux); cudaFree(S->work); cudaFree(S->scal); cudaFree(S->counters);
-        delete S->dots;
+        cudaFree(S->aux); cudaFree(S->work); cudaFree(S->scal); cudaFree(S->counters); cudaFree(S->part);
         delete S;
         return e;
     };
     if ((st = dalloc(&S->aux, (size_t)n)) || (st = dalloc(&S->work, (size_t)3 * n)) || (st = dalloc(&S->scal, 8)) ||
-        (st = dalloc(&S->counters, 2)) || (st = S->dots->init(3, 1)))
+        (st = dalloc(&S->counters, 2)) || (st = dalloc(&S->part, (size_t)2 * stage_blocks(n))))
         return fail(st);
     k_f64_to_bf16_scaled<<<grid_for(n), kThreads>>>(n, aux, aux_scale, S->aux);
     count_launch();
     if (cudaMemset(S->counters, 0, 2 * sizeof(int)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
         return fail(cuda_error(cudaGetLastError(), "stage_create"));
     *out = S;
+    return HEC_OK;
+}
+
+HEC_API hec_status stage_apply(const hec_stage* stage, const double* v, double* z, void* stream) {
+    clear_error();
+    if (!stage || !v || !z) return set_error(HEC_ERR_INVALID_ARG, "stage_apply: NULL");
+    HEC_CHECK(stage_run(stage, v, z, nullptr, S(stream)));
+    HEC_CUDA(cudaGetLastError());
     return HEC_OK;
 }
 
@@ -523,7 +676,7 @@ HEC_API hec_status stage_destroy(hec_stage* S) {
     cudaFree(S->work);
     cudaFree(S->scal);
     cudaFree(S->counters);
-    delete S->dots;
+    cudaFree(S->part);
     delete S;
     return HEC_OK;
 }
@@ -674,11 +827,12 @@ HEC_API hec_status fgmres_solve(const hec_matrix* A, const ilu_precond* M, const
             double* wv = W.V + (long)(j + 1) * nk;
             if (M) {
                 HEC_CHECK(ilu_apply(M, K, vj, K, zj, K, stream));
-                if (extra) HEC_CHECK(stage_apply(extra, vj, zj, s));
+                // a stage on this same matrix also returns w = A z_j
+                if (extra) HEC_CHECK(stage_run(extra, vj, zj, extra->A == A ? wv : nullptr, s));
             } else {
                 HEC_CUDA(cudaMemcpyAsync(zj, vj, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
             }
-            HEC_CHECK(spmv_impl(A, K, 1.0, zj, K, 0.0, wv, K, s));
+            if (!extra || extra->A != A) HEC_CHECK(spmv_impl(A, K, 1.0, zj, K, 0.0, wv, K, s));
             // modified Gram-Schmidt, ||w||, Hessenberg column, rotations, w /= h_{j+1,j}
             HEC_CHECK(mgs.run(n, K, j, m, rtol, W.V, nk, wv, as, s));
             HEC_CUDA(cudaMemcpyAsync(W.pinned + (j & 1), as.any, sizeof(int), cudaMemcpyDeviceToHost, s));

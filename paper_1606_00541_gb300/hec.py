@@ -415,6 +415,7 @@ _net_train_step = _sig("net_train_step", _vp, _i, _i, _i, _i, _vp, _vp, ctypes.c
                        ctypes.POINTER(ctypes.c_float), _vp)
 _stage_create = _sig("stage_create", _vp, _vp, _i, _i, _i, _vp, _d, _d, ctypes.POINTER(_vp))
 _stage_stats = _sig("stage_stats", _vp, ctypes.POINTER(_i), ctypes.POINTER(_i), _i)
+_stage_apply = _sig("stage_apply", _vp, _vp, _vp, _vp)
 _stage_destroy = _sig("stage_destroy", _vp)
 
 
@@ -480,6 +481,12 @@ class Stage(_Handle):
         a, b = _i(), _i()
         _check(_stage_stats(self.h, ctypes.byref(a), ctypes.byref(b), 1 if reset else 0), "stage_stats")
         return dict(applied=a.value, accepted=b.value)
+
+    def apply(self, v, z1, stream=None):
+        """z = z1 + alpha c or z1 (see stage_apply); v, z1 device FP64 [n]; z1 is left unchanged."""
+        z = z1.clone()
+        _check(_stage_apply(self.h, _ptr(v), _ptr(z), _stream(stream)), "stage_apply")
+        return z
 
 
 _ras_setup = _sig("ras_setup", _i, _vp, _vp, _vp, _vp, _i, ctypes.POINTER(_vp), _vp)

@@ -72,10 +72,19 @@ def lognormal_perm(m, sigma=2.0, seed=0):
 
 
 def fv7_lognormal(m, sigma=2.0, seed=0, perm=None):
-    n, g, x, y, z = _grid3(m)
-    k = lognormal_perm(m, sigma, seed) if perm is None else np.asarray(perm, dtype=np.float64)
-    s = m * m
-    nbr = [(-s, z > 0), (-m, y > 0), (-1, x > 0), (1, x < m - 1), (m, y < m - 1), (s, z < m - 1)]
+    k = lognormal_perm(m, sigma, seed) if perm is None else perm
+    return fv7_lognormal_box(m, m, m, perm=k)
+
+
+def fv7_lognormal_box(nx, ny, nz, perm):
+    """7-point finite-volume matrix on an nx x ny x nz grid (x fastest) for cell permeability
+    `perm`: harmonic face averages, Dirichlet faces at the boundary (2 k)."""
+    n = nx * ny * nz
+    g = np.arange(n, dtype=np.int64)
+    x, y, z = g % nx, (g // nx) % ny, g // (nx * ny)
+    k = np.asarray(perm, dtype=np.float64)
+    s = nx * ny
+    nbr = [(-s, z > 0), (-nx, y > 0), (-1, x > 0), (1, x < nx - 1), (nx, y < ny - 1), (s, z < nz - 1)]
     diag = np.zeros(n)
     off_vals = []
     for o, ok in nbr:
@@ -84,7 +93,7 @@ def fv7_lognormal(m, sigma=2.0, seed=0, perm=None):
         tb = np.where(ok, 0.0, 2.0 * k)                      # Dirichlet boundary face
         diag += t + tb
         off_vals.append(-t)
-    cols = np.stack([g - s, g - m, g - 1, g, g + 1, g + m, g + s], axis=1)
+    cols = np.stack([g - s, g - nx, g - 1, g, g + 1, g + nx, g + s], axis=1)
     vals = np.stack(off_vals[:3] + [diag] + off_vals[3:], axis=1)
     mask = np.stack([nbr[0][1], nbr[1][1], nbr[2][1], np.ones(n, bool), nbr[3][1], nbr[4][1], nbr[5][1]], axis=1)
     return _assemble(cols, vals, mask)

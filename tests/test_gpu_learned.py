@@ -221,3 +221,49 @@ def test_trained_stage_gain(hec):
                                        tinfo["loss_first"], tinfo["loss_last"]))
     assert learned["converged"]
     assert learned["iterations"] <= plain["iterations"]
+
+
+def test_stage_apply_matches_its_definition(hec):
+    """One stage application against the stage's definition assembled from separate calls: r1 =
+    v - A z1, sigma = RMS(r1), c = sigma Net([r1 / sigma, aux / 2]) (the network run on the packed
+    sample of net_make_sample), alpha = <r1, Ac> / <Ac, Ac>, z = z1 + alpha c.  The stage reads r1
+    and aux directly in its first layer and writes c from its last, so this checks the fused
+    input and output paths; an x extent of 37 leaves a ragged 32-wide tile."""
+    import ctypes
+    from paper_1606_00541_gb300 import learn
+    dims = (37, 20, 18)
+    n = int(np.prod(dims))
+    lnk = np.random.default_rng(np.random.PCG64(31)).normal(0.0, 2.0, size=n)
+    nx, ny, nz = dims
+    A = synth.fv7_lognormal_box(nx, ny, nz, perm=np.exp(lnk))
+    Ad = [torch.as_tensor(a, device="cuda") for a in A]
+    Lh, Uh = hec.ilu_factor(*Ad, k=0)
+    s = hec.IluSolver(Lh.tensors(), Uh.tensors(), A=Ad, vdt="f32")
+    net = hec.Net(learn.init_params(4, last_scale=1.0))
+    aux = torch.as_tensor(lnk, device="cuda")
+    v = torch.as_tensor(synth.uniform_vector(n, 8), device="cuda")
+    z1 = s.apply(v)
+    stage = hec.Stage(net, s.A, dims, aux, rho=1e12)
+    z = stage.apply(v, z1)
+    # the definition, one call at a time
+    r1 = hec.spmv(s.A, z1, v.clone(), alpha=-1.0, beta=1.0)
+    x = torch.empty(n, C, dtype=torch.bfloat16, device="cuda")
+    sig = torch.empty(1, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    hec._check(hec._lib.net_make_sample(ctypes.c_int(n), ctypes.c_void_p(r1.data_ptr()), None,
+                                        ctypes.c_void_p(aux.data_ptr()), ctypes.c_double(0.5),
+                                        ctypes.c_void_p(x.data_ptr()), None, ctypes.c_void_p(sig.data_ptr()),
+                                        ctypes.c_void_p(st)), "net_make_sample")
+    out = net.forward(x, dims)
+    c = sig * out.double()
+    Ac = hec.spmv(s.A, c)
+    alpha = float(torch.dot(r1, Ac) / torch.dot(Ac, Ac))
+    assert alpha > 0.0
+    zr = z1 + alpha * c
+    # the stage takes alpha's inner products with FP32 partial sums: alpha within ~1e-6
+    tol = 1e-5 * float(torch.max(torch.abs(alpha * c))) + 1e-12 * float(torch.max(torch.abs(zr)))
+    assert float(torch.max(torch.abs(z - zr))) <= tol
+    assert stage.stats()["accepted"] == 1
+    # the fallback returns z1 itself
+    never = hec.Stage(net, s.A, dims, aux, rho=1e-12)
+    assert torch.equal(never.apply(v, z1), z1)
