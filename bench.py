@@ -13,8 +13,10 @@ Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle instead 
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -49,6 +51,34 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+SWEEP_PROFILE = os.path.join(ROOT, "profiles", "k_sweep_fv7_128cubed_ilu0_f32.md")
+SWEEP_SOURCES = ("paper_1606_00541_gb300/csrc/sweep.cu", "paper_1606_00541_gb300/csrc/sync.cuh",
+                 "paper_1606_00541_gb300/csrc/internal.cuh")
+
+
+def sweep_source_digest():
+    """First 16 hex digits of the SHA-256 of the sweep kernel's sources."""
+    h = hashlib.sha256()
+    for p in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes (read + write) per sweep launch from the committed ncu capture of this workload,
+    or None when the sweep's sources have changed since that capture."""
+    try:
+        with open(SWEEP_PROFILE) as f:
+            text = f.read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*(\d+)\s+source_digest:\s*([0-9a-f]+)", text)
+    if not m or m.group(2) != sweep_source_digest():
+        return None
+    return int(m.group(1))
 
 
 def sweep_bytes(nnz, n, k, sv):
@@ -261,7 +291,8 @@ def main():
     achieved = per_sweep / avg_launch_s / 1e9
     step_s = elapsed / args.steps
     roofline = {"bound": "hbm", "kernel": "k_sweep<float,float,1>", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": recorded_traffic(), "traffic_unit": "bytes/launch",
+                "peak_source": src,
                 "sweep_share_of_step": (sweep_ms / 1000.0) / elapsed,
                 "avg_sweep_us": avg_launch_s * 1e6, "bytes_per_sweep": per_sweep}
 
