@@ -364,6 +364,11 @@ typedef struct hec_ras hec_ras;
  * nsub * n < 2^31.  Synchronizes `stream`. */
 hec_status ras_setup(int n, const int* rowptr, const int* col, const double* val, const int* part,
                      int nsub, hec_ras** out, void* stream);
+/* The same with the overlap chosen: 1 as ras_setup; 0 keeps each subdomain to its owned rows,
+ * which makes ilu_apply block ILU(0) (block Jacobi with ILU(0) blocks, the paper's BILU).  Any
+ * other overlap returns HEC_ERR_INVALID_ARG. */
+hec_status ras_setup_overlap(int n, const int* rowptr, const int* col, const double* val,
+                             const int* part, int nsub, int overlap, hec_ras** out, void* stream);
 hec_status hec_ras_get(const hec_ras* R, int* n_ext, const int** ext_ptr, const int** ext2glob,
                        const unsigned char** owned, const hec_csr** A_ext);
 hec_status hec_ras_destroy(hec_ras* R);

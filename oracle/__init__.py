@@ -325,10 +325,19 @@ def block_diag(blocks):
             np.concatenate(vs) if vs else np.zeros(0))
 
 
-def ras_setup(A, part, ns):
-    """Extended subdomains (overlap 1), A_s = A[ext, ext], ILU(0) of each, assembled as one
-    block-diagonal pair of factors (Eq. 4)."""
-    ptr, idx = ras_extend(A, part, ns)
+def owned_sets(part, ns):
+    """Subdomains without overlap: ext(s) = {i : part[i] = s} in ascending order."""
+    part = _i32(part)
+    idx = np.concatenate([np.flatnonzero(part == s) for s in range(ns)]).astype(np.int32)
+    ptr = np.zeros(ns + 1, dtype=np.int32)
+    ptr[1:] = np.cumsum(np.bincount(part, minlength=ns))
+    return ptr, idx
+
+
+def ras_setup(A, part, ns, overlap=1):
+    """Extended subdomains (overlap 1; overlap 0 keeps the owned rows: block ILU), A_s =
+    A[ext, ext], ILU(0) of each, assembled as one block-diagonal pair of factors (Eq. 4)."""
+    ptr, idx = ras_extend(A, part, ns) if overlap else owned_sets(part, ns)
     Ls, Us = [], []
     for s in range(ns):
         As = submatrix(A, idx[ptr[s]:ptr[s + 1]])

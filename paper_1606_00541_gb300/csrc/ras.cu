@@ -2,7 +2,8 @@
 //
 // Each subdomain s owns the rows i with part[i] == s.  Its extended set adds every column of an
 // owned row (overlap 1: the subdomain "extended according to the topology of the graph"), in
-// ascending global index.  A_s = A restricted to the extended rows and columns, and all A_s are
+// ascending global index; with overlap 0 it is the owned set itself, which gives block ILU(0)
+// (block Jacobi with ILU(0) blocks).  A_s = A restricted to the extended rows and columns, and all A_s are
 // assembled as ONE block-diagonal matrix diag(A_1, ..., A_s) over the n_ext extended rows, so
 // that a single ILU(0), a single level analysis and a single pair of sweeps serve every
 // subdomain at once (Eq. 4).  ext2glob maps extended rows to global rows and owned marks the
@@ -35,13 +36,13 @@ __global__ void k_check_part(int n, const int* __restrict__ part, int nsub, int*
     if (i < n && (part[i] < 0 || part[i] >= nsub)) atomicCAS(code, 0, 1);
 }
 
-__global__ void k_pair_counts(int n, const int* __restrict__ rp, int* cnt) {
+__global__ void k_pair_counts(int n, const int* __restrict__ rp, int overlap, int* cnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) cnt[i] = 1 + rp[i + 1] - rp[i];
+    if (i < n) cnt[i] = 1 + (overlap ? rp[i + 1] - rp[i] : 0);
 }
 
 __global__ void k_pairs(int n, const int* __restrict__ rp, const int* __restrict__ col, const int* __restrict__ part,
-                        const int* __restrict__ off, int* keys, int* vals) {
+                        int overlap, const int* __restrict__ off, int* keys, int* vals) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int base = part[i] * n;
@@ -49,6 +50,7 @@ __global__ void k_pairs(int n, const int* __restrict__ rp, const int* __restrict
     keys[o] = base + i;
     vals[o] = o;
     ++o;
+    if (!overlap) return;
     for (int p = rp[i]; p < rp[i + 1]; ++p, ++o) {
         keys[o] = base + col[p];
         vals[o] = o;
@@ -128,11 +130,13 @@ void free_ras(hec_ras* R) {
 
 using namespace hec;
 
-HEC_API hec_status ras_setup(int n, const int* rowptr, const int* col, const double* val, const int* part, int nsub,
-                             hec_ras** out, void* stream) {
+HEC_API hec_status ras_setup_overlap(int n, const int* rowptr, const int* col, const double* val, const int* part,
+                                     int nsub, int overlap, hec_ras** out, void* stream) {
     clear_error();
-    if (!out || n <= 0 || nsub < 1 || !rowptr || !col || !val || !part || (long long)nsub * n > 0x7fffffffLL)
-        return set_error(HEC_ERR_INVALID_ARG, "ras_setup: bad argument (nsub * n must stay below 2^31)");
+    if (!out || n <= 0 || nsub < 1 || !rowptr || !col || !val || !part || (long long)nsub * n > 0x7fffffffLL ||
+        (overlap != 0 && overlap != 1))
+        return set_error(HEC_ERR_INVALID_ARG,
+                         "ras_setup: bad argument (nsub * n must stay below 2^31, overlap 0 or 1)");
     *out = nullptr;
     cudaStream_t s = S(stream);
     HEC_CHECK(validate_csr(n, rowptr, col, -1, s));
@@ -163,7 +167,7 @@ HEC_API hec_status ras_setup(int n, const int* rowptr, const int* col, const dou
     if (h) return fail(set_error(HEC_ERR_INVALID_ARG, "ras_setup: part[] outside [0, nsub)"));
     // (subdomain, row) pairs of every owned row and its columns
     if ((st = dalloc(&cnt, (size_t)n + 1)) || (st = dalloc(&off, (size_t)n + 1))) return fail(st);
-    k_pair_counts<<<g, 256, 0, s>>>(n, rowptr, cnt);
+    k_pair_counts<<<g, 256, 0, s>>>(n, rowptr, overlap, cnt);
     count_launch();
     if ((st = exclusive_scan_i32(cnt, off, n, true, s))) return fail(st);
     int m = 0;
@@ -171,7 +175,7 @@ HEC_API hec_status ras_setup(int n, const int* rowptr, const int* col, const dou
     if ((st = dalloc(&keys, (size_t)m)) || (st = dalloc(&vals, (size_t)m)) || (st = dalloc(&flag, (size_t)m + 1)) ||
         (st = dalloc(&pos, (size_t)m + 1)))
         return fail(st);
-    k_pairs<<<g, 256, 0, s>>>(n, rowptr, col, part, off, keys, vals);
+    k_pairs<<<g, 256, 0, s>>>(n, rowptr, col, part, overlap, off, keys, vals);
     count_launch();
     if ((st = sort_pairs_i32(keys, vals, m, nsub * n - 1, s))) return fail(st);
     const int gm = (m + 255) / 256;
@@ -208,6 +212,11 @@ HEC_API hec_status ras_setup(int n, const int* rowptr, const int* col, const dou
     cleanup();
     *out = R;
     return HEC_OK;
+}
+
+HEC_API hec_status ras_setup(int n, const int* rowptr, const int* col, const double* val, const int* part, int nsub,
+                             hec_ras** out, void* stream) {
+    return ras_setup_overlap(n, rowptr, col, val, part, nsub, 1, out, stream);
 }
 
 HEC_API hec_status hec_ras_get(const hec_ras* R, int* n_ext, const int** ext_ptr, const int** ext2glob,

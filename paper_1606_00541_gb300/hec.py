@@ -490,6 +490,7 @@ class Stage(_Handle):
 
 
 _ras_setup = _sig("ras_setup", _i, _vp, _vp, _vp, _vp, _i, ctypes.POINTER(_vp), _vp)
+_ras_setup_overlap = _sig("ras_setup_overlap", _i, _vp, _vp, _vp, _vp, _i, _i, ctypes.POINTER(_vp), _vp)
 _hec_ras_get = _sig("hec_ras_get", _vp, ctypes.POINTER(_i), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                     ctypes.POINTER(_vp), ctypes.POINTER(_vp))
 _hec_ras_destroy = _sig("hec_ras_destroy", _vp)
@@ -523,11 +524,12 @@ class Ras(_Handle):
                  _view(q[2].value, nnz.value, torch.float64, self).clone()))
 
 
-def ras_setup(rowptr, col, val, part, nsub, stream=None):
+def ras_setup(rowptr, col, val, part, nsub, stream=None, overlap=1):
+    """Subdomain system (ras_setup_overlap): overlap 1 = RAS, overlap 0 = block ILU."""
     n = rowptr.numel() - 1
     out = _vp()
-    _check(_ras_setup(n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(part), int(nsub), ctypes.byref(out),
-                      _stream(stream)), "ras_setup")
+    _check(_ras_setup_overlap(n, _ptr(rowptr), _ptr(col), _ptr(val), _ptr(part), int(nsub), int(overlap),
+                              ctypes.byref(out), _stream(stream)), "ras_setup_overlap")
     return Ras(out.value)
 
 
@@ -569,10 +571,11 @@ class IluSolver:
 class RasSolver(IluSolver):
     """RAS preconditioner (Sec. 3, Eq. 4): ras_setup on the GPU, ILU(0) of the block-diagonal
     subdomain system, one pair of batched sweeps for all subdomains, restricted write-back.
-    Pass `factors=(L, U)` to use given block-diagonal factors instead of the GPU ILU(0)."""
+    Pass `factors=(L, U)` to use given block-diagonal factors instead of the GPU ILU(0);
+    overlap=0 gives block ILU (block Jacobi with ILU blocks)."""
 
-    def __init__(self, A, part, nsub, vdt="f32", max_nrhs=1, stream=None, factors=None, **tune):
-        self.R = ras_setup(*A, part, nsub, stream)
+    def __init__(self, A, part, nsub, vdt="f32", max_nrhs=1, stream=None, factors=None, overlap=1, **tune):
+        self.R = ras_setup(*A, part, nsub, stream, overlap=overlap)
         self.ext_ptr, self.ext2glob, self.owned, self.A_ext = self.R.tensors(nsub)
         if factors is None:
             Lh, Uh = ilu_factor(*self.A_ext, k=0, stream=stream)

@@ -489,6 +489,27 @@ def test_ras_with_exact_local_solves_matches_dense_definition(orc):
     assert np.max(np.abs(z - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
+def test_block_ilu_on_tridiagonal_blocks_is_block_jacobi(orc):
+    """Overlap 0 (the paper's block ILU): each subdomain keeps its owned rows; on a tridiagonal
+    matrix ILU(0) of every diagonal block is its exact LU, so the apply equals block Jacobi,
+    z_s = A[s, s]^-1 v_s, written out densely."""
+    n = 40
+    D = np.diag(np.full(n, 2.5)) + np.diag(np.full(n - 1, -1.0), 1) + np.diag(np.full(n - 1, -1.1), -1)
+    A = csr_of(D)
+    part = np.array([0] * 7 + [2] * 13 + [1] * 9 + [0] * 11, dtype=np.int32)  # block 0 not contiguous
+    R = orc.ras_setup(A, part, 3, overlap=0)
+    ptr, idx = R["ext_ptr"], R["ext_idx"]
+    for s in range(3):
+        assert list(idx[ptr[s]:ptr[s + 1]]) == list(np.flatnonzero(part == s))
+    v = synth.uniform_vector(n, 6)
+    z = orc.ras_apply(R, v)
+    ref = np.zeros(n)
+    for s in range(3):
+        e = np.flatnonzero(part == s)
+        ref[e] = np.linalg.solve(D[np.ix_(e, e)], v[e])
+    assert np.max(np.abs(z - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
 # --- FGMRES --------------------------------------------------------------------------------
 
 def test_fgmres_unrestarted_matches_dense_solve(orc):
