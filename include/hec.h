@@ -342,6 +342,13 @@ hec_status hec_csr_destroy(hec_csr* M);
  * Rows run in the level order of the lower pattern with point-to-point completion waits.
  * Outputs L (unit lower, the 1.0 diagonal stored) and U (upper with its diagonal).  A must have
  * a nonzero diagonal in every row; ZERO_PIVOT if an eliminated pivot is zero.  Synchronizes. */
+/* The lower (uplo 0: j <= i) or upper (uplo 1: j >= i) triangle of a CSR matrix (n x n,
+ * ascending columns), without the diagonal when strict != 0, as a device CSR owned by the
+ * library.  With it the sweeps run Gauss-Seidel: one forward sweep is (D + L) x' = b - U_s x,
+ * one backward sweep (D + U) x'' = b - L_s x' (the smoothers the paper names as another use of
+ * the triangular solver, Sec. 1).  Synchronizes `stream`. */
+hec_status csr_triangle(int n, const int* rowptr, const int* col, const double* val, int uplo,
+                        int strict, hec_csr** out, void* stream);
 hec_status ilu_factor(int n, const int* rowptr, const int* col, const double* val, int k,
                       hec_csr** L, hec_csr** U, void* stream);
 

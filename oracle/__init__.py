@@ -356,6 +356,31 @@ def ras_apply(R, v):
     return z
 
 
+# --- Gauss-Seidel smoother (Sec. 1: the smoother use of triangular solves) -----------------------
+
+def sgs(A, b, x0, sweeps=1):
+    """Symmetric Gauss-Seidel, written from its definition: a forward sweep updates x_i, i = 0..n-1,
+    to (b_i - sum_{j != i} a_ij x_j) / a_ii with the newest values, then a backward sweep does the
+    same for i = n-1..0.  Plain loops (small cases only)."""
+    rp, ci, v = _i32(A[0]), _i32(A[1]), _f64(A[2])
+    n = len(rp) - 1
+    x = _f64(x0).copy()
+    b = _f64(b)
+    for _ in range(sweeps):
+        for order in (range(n), range(n - 1, -1, -1)):
+            for i in order:
+                s = b[i]
+                d = 0.0
+                for p in range(rp[i], rp[i + 1]):
+                    j = ci[p]
+                    if j == i:
+                        d = v[p]
+                    else:
+                        s -= v[p] * x[j]
+                x[i] = s / d
+    return x
+
+
 # --- FGMRES ---------------------------------------------------------------------------------
 
 def _fgmres_out(rc, x, info, hist):

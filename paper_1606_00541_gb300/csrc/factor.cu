@@ -196,6 +196,72 @@ HEC_API hec_status hec_csr_get(const hec_csr* M, int* n, long long* nnz, const i
     return HEC_OK;
 }
 
+namespace hec {
+namespace {
+// keep (i, j) when j <= i (uplo 0) or j >= i (uplo 1), the diagonal excluded when strict
+__device__ __forceinline__ bool keep_entry(int i, int j, int uplo, int strict) {
+    return uplo == 0 ? (strict ? j < i : j <= i) : (strict ? j > i : j >= i);
+}
+__global__ void k_tri_count(int n, const int* __restrict__ rp, const int* __restrict__ col, int uplo, int strict,
+                            int* __restrict__ len) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = 0;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) c += keep_entry(i, col[p], uplo, strict);
+    len[i] = c;
+}
+__global__ void k_tri_fill(int n, const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+                           int uplo, int strict, const int* __restrict__ orp, int* __restrict__ ocol,
+                           double* __restrict__ oval) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int o = orp[i];
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+        if (keep_entry(i, col[p], uplo, strict)) {
+            ocol[o] = col[p];
+            oval[o] = val[p];
+            ++o;
+        }
+}
+}  // namespace
+}  // namespace hec
+
+HEC_API hec_status csr_triangle(int n, const int* rowptr, const int* col, const double* val, int uplo, int strict,
+                                hec_csr** out, void* stream) {
+    clear_error();
+    if (!out || n < 0 || (uplo != 0 && uplo != 1) || (n > 0 && (!rowptr || !col || !val)))
+        return set_error(HEC_ERR_INVALID_ARG, "csr_triangle: bad argument");
+    *out = nullptr;
+    cudaStream_t s = S(stream);
+    HEC_CHECK(validate_csr(n, rowptr, col, -1, s));
+    hec_csr* T = new hec_csr();
+    T->n = n;
+    int* len = nullptr;
+    hec_status st = HEC_OK;
+    auto fail = [&](hec_status e) {
+        cudaFree(len);
+        free_csr(T);
+        return e;
+    };
+    if ((st = dalloc(&len, (size_t)n + 1)) || (st = dalloc(&T->rowptr, (size_t)n + 1))) return fail(st);
+    const int g = std::max(1, (n + 255) / 256);
+    if (n > 0) k_tri_count<<<g, 256, 0, s>>>(n, rowptr, col, uplo, strict, len);
+    count_launch();
+    if ((st = exclusive_scan_i32(len, T->rowptr, n, true, s))) return fail(st);
+    int nnz = 0;
+    HEC_CUDA(cudaMemcpyAsync(&nnz, T->rowptr + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HEC_CUDA(cudaStreamSynchronize(s));
+    T->nnz = nnz;
+    if ((st = dalloc(&T->col, (size_t)std::max(nnz, 1))) || (st = dalloc(&T->val, (size_t)std::max(nnz, 1))))
+        return fail(st);
+    if (n > 0) k_tri_fill<<<g, 256, 0, s>>>(n, rowptr, col, val, uplo, strict, T->rowptr, T->col, T->val);
+    count_launch();
+    HEC_CUDA(cudaGetLastError());
+    cudaFree(len);
+    *out = T;
+    return HEC_OK;
+}
+
 HEC_API hec_status hec_csr_destroy(hec_csr* M) {
     free_csr(M);
     return HEC_OK;

@@ -405,6 +405,47 @@ def ilu_factor(rowptr, col, val, k=0, stream=None):
     return Csr(L.value), Csr(U.value)
 
 
+_csr_triangle = _sig("csr_triangle", _i, _vp, _vp, _vp, _i, _i, ctypes.POINTER(_vp), _vp)
+
+
+def csr_triangle(rowptr, col, val, uplo, strict=False, stream=None):
+    """Lower (uplo 0) or upper (uplo 1) triangle of a device CSR matrix, without the diagonal
+    when strict (csr_triangle)."""
+    n = rowptr.numel() - 1
+    out = _vp()
+    _check(_csr_triangle(n, _ptr(rowptr), _ptr(col), _ptr(val), int(uplo), 1 if strict else 0, ctypes.byref(out),
+                         _stream(stream)), "csr_triangle")
+    return Csr(out.value)
+
+
+class SgsSmoother:
+    """Symmetric Gauss-Seidel on the level-scheduled sweeps (the smoother use of the triangular
+    solver, Sec. 1): a forward sweep solves (D + L) x' = b - U_s x, a backward sweep
+    (D + U) x'' = b - L_s x'.  Level scheduling only reorders independent rows, so every sweep
+    equals the sequential Gauss-Seidel sweep up to rounding."""
+
+    def __init__(self, A, vdt="f64", max_nrhs=1, stream=None):
+        DL, Us = csr_triangle(*A, 0, False, stream).tensors(), csr_triangle(*A, 1, True, stream).tensors()
+        DU, Ls = csr_triangle(*A, 1, False, stream).tensors(), csr_triangle(*A, 0, True, stream).tensors()
+        self.lvL = sptrsv_analyze(DL[0], DL[1], 0, stream)
+        self.lvU = sptrsv_analyze(DU[0], DU[1], 1, stream)
+        self.pL = sptrsv_plan_create(hec_from_csr(*DL, levels=self.lvL, vdt=vdt, stream=stream), self.lvL, max_nrhs)
+        self.pU = sptrsv_plan_create(hec_from_csr(*DU, levels=self.lvU, vdt=vdt, stream=stream), self.lvU, max_nrhs)
+        self.Us = hec_from_csr(*Us, vdt="f64", stream=stream)
+        self.Ls = hec_from_csr(*Ls, vdt="f64", stream=stream)
+
+    def smooth(self, x, b, sweeps=1, stream=None):
+        """`sweeps` symmetric Gauss-Seidel sweeps from x (device FP64 [n] or [n, k]); returns the
+        new iterate (x is not modified)."""
+        r = torch.empty_like(b)
+        for _ in range(sweeps):
+            r.copy_(b)
+            x = sptrsv_lower(self.pL, spmv(self.Us, x, r, alpha=-1.0, beta=1.0, stream=stream), stream=stream)
+            r.copy_(b)
+            x = sptrsv_upper(self.pU, spmv(self.Ls, x, r, alpha=-1.0, beta=1.0, stream=stream), stream=stream)
+        return x
+
+
 _lib.net_param_count.restype = _i
 _net_create = _sig("net_create", _vp, ctypes.POINTER(_vp))
 _net_destroy = _sig("net_destroy", _vp)

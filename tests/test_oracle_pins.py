@@ -510,6 +510,50 @@ def test_block_ilu_on_tridiagonal_blocks_is_block_jacobi(orc):
     assert np.max(np.abs(z - ref)) <= 1e-13 * np.max(np.abs(ref))
 
 
+# --- symmetric Gauss-Seidel (the smoother use of the sweeps) ----------------------------------
+
+def test_sgs_matches_the_matrix_splitting(orc):
+    """The loops against the splitting A = L_s + D + U_s written with dense solves:
+    x' = (D + L_s)^-1 (b - U_s x0), x'' = (D + U_s)^-1 (b - L_s x')."""
+    A = synth.random_sparse(50, 0.1, 9, dominance=1.5)
+    D = dense(A)
+    b = synth.uniform_vector(50, 2)
+    x0 = synth.uniform_vector(50, 3)
+    Ls, Us, Dg = np.tril(D, -1), np.triu(D, 1), np.diag(np.diag(D))
+    x1 = np.linalg.solve(Dg + Ls, b - Us @ x0)
+    x2 = np.linalg.solve(Dg + Us, b - Ls @ x1)
+    assert np.max(np.abs(orc.sgs(A, b, x0, 1) - x2)) <= 1e-12 * np.max(np.abs(x2))
+
+
+def test_sgs_special_cases(orc):
+    # lower triangular: the forward sweep is the exact solve and the backward sweep keeps it
+    L = orc.ilu0(synth.fv7_lognormal(4, seed=3))[0]
+    b = synth.uniform_vector(64, 4)
+    ref = sla.solve_triangular(dense(L), b, lower=True)
+    assert np.max(np.abs(orc.sgs(L, b, np.zeros(64), 1) - ref)) <= 1e-13 * np.max(np.abs(ref))
+    # diagonal: one sweep divides by the diagonal
+    d = np.linspace(1.0, 3.0, 10)
+    Dm = csr_of(np.diag(d))
+    assert np.array_equal(orc.sgs(Dm, np.ones(10), np.zeros(10), 1), 1.0 / d)
+
+
+def test_sgs_converges_in_the_energy_norm(orc):
+    """For SPD A each symmetric sweep is a contraction in the A-norm of the error."""
+    A = synth.poisson2d_5pt(8)
+    D = dense(A)
+    b = synth.uniform_vector(64, 5)
+    xs = np.linalg.solve(D, b)
+    x = np.zeros(64)
+    prev = np.inf
+    for _ in range(100):
+        x = orc.sgs(A, b, x, 1)
+        e = x - xs
+        en = float(e @ D @ e)
+        assert en < prev or en < 1e-28
+        prev = en
+    assert np.max(np.abs(x - xs)) <= 1e-8 * np.max(np.abs(xs))
+
+
 # --- FGMRES --------------------------------------------------------------------------------
 
 def test_fgmres_unrestarted_matches_dense_solve(orc):
