@@ -5,6 +5,8 @@ One step = one pass of the whole hot path over the workload: level analysis of L
 HEC packing of L, U and A (Sec. 2.1, Alg. 1), solve plans, and an ILU(0)-preconditioned FGMRES(30)
 solve of A x = b to a 1e-8 relative residual (FP32 factor values, FP64 outer loop), whose every
 inner iteration runs the lower and upper sweeps (Alg. 2), SpMV and the Gram-Schmidt kernels.  The
+sweeps run partitioned by default (`--sweep part`: 144 x-pencils of the grid, one 1024-thread block
+each, same results up to summation order); `--sweep global` times the global level-ordered kernel.  The
 ILU(0) factors are computed once on the GPU before timing.  Inputs are seeded and synthetic
 (ln k ~ N(0, 2^2), b = A x_true with x_true ~ U[-1, 1]); the working set (~1 GB) is larger than L2.
 
@@ -53,7 +55,8 @@ def peaks():
         return 6800.0, "fallback"
 
 
-SWEEP_PROFILE = os.path.join(ROOT, "profiles", "k_sweep_fv7_128cubed_ilu0_f32.md")
+SWEEP_PROFILES = {"global": os.path.join(ROOT, "profiles", "k_sweep_fv7_128cubed_ilu0_f32.md"),
+                  "part": os.path.join(ROOT, "profiles", "k_sweep_part_fv7_128cubed_pencils_f32.md")}
 SWEEP_SOURCES = ("paper_1606_00541_gb300/csrc/sweep.cu", "paper_1606_00541_gb300/csrc/sync.cuh",
                  "paper_1606_00541_gb300/csrc/internal.cuh")
 
@@ -67,11 +70,11 @@ def sweep_source_digest():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes (read + write) per sweep launch from the committed ncu capture of this workload,
-    or None when the sweep's sources have changed since that capture."""
+def recorded_traffic(schedule):
+    """DRAM bytes (read + write) per sweep launch from the committed ncu capture of this workload
+    and sweep schedule, or None when the sweep's sources have changed since that capture."""
     try:
-        with open(SWEEP_PROFILE) as f:
+        with open(SWEEP_PROFILES[schedule]) as f:
             text = f.read()
     except OSError:
         return None
@@ -216,6 +219,8 @@ def main():
     ap.add_argument("--cfg4", action="store_true", help="also run the 200^3 learned-stage comparison")
     ap.add_argument("--ref-iters", type=int, default=150, help="iteration count used to scale the oracle sample")
     ap.add_argument("--ref-sample-iters", type=int, default=8)
+    ap.add_argument("--sweep", default="part", choices=["part", "global"],
+                    help="single-RHS sweep schedule of the timed step: x-pencil partitioned (default) or global")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -248,8 +253,12 @@ def main():
     L, U = Lh.tensors(), Uh.tensors()
     nnzL, nnzU = L[1].numel(), U[1].numel()
 
+    part_d, nparts = sweep_partition(torch, m, devn)
+
     def step(vdt="f32", Lf=L, Uf=U, b=bd, A_=Ad):
         s = hec.IluSolver(Lf, Uf, A=A_, vdt=vdt)
+        if args.sweep == "part":
+            s.partition(part_d, nparts, threads=PART_THREADS)
         x, info = s.solve(b, restart=RESTART, rtol=RTOL, max_iters=5000)
         return x, info, s
 
@@ -290,8 +299,9 @@ def main():
     avg_launch_s = (sweep_ms / 1000.0) / max(sweep_launches, 1)
     achieved = per_sweep / avg_launch_s / 1e9
     step_s = elapsed / args.steps
-    roofline = {"bound": "hbm", "kernel": "k_sweep<float,float,1>", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": recorded_traffic(), "traffic_unit": "bytes/launch",
+    kname = "k_sweep_part<float,float,4>" if args.sweep == "part" else "k_sweep<float,float,1>"
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": recorded_traffic(args.sweep), "traffic_unit": "bytes/launch",
                 "peak_source": src,
                 "sweep_share_of_step": (sweep_ms / 1000.0) / elapsed,
                 "avg_sweep_us": avg_launch_s * 1e6, "bytes_per_sweep": per_sweep}
@@ -323,13 +333,15 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (about 1 GB working set)"},
             "fgmres_iterations": its, "true_rel_residual": relres, "factor_s": factor_s,
+            "sweep_schedule": ("x-pencil partitioned: %d parts, %d threads per part" % (nparts, PART_THREADS)
+                               if args.sweep == "part" else "global level-ordered"),
             "roofline": roofline,
             "e2e": {"value": world * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": n * 8},
             "gpu_launches": launches, "clocks": clk}
 
     if rank == 0 and not args.no_variants:
-        line["variants"] = variants(hec, torch, Ad, L, U, bd, HA0, n, nnzL, nnzU, hbm)
+        line["variants"] = variants(hec, torch, Ad, L, U, bd, HA0, n, nnzL, nnzU, hbm, (part_d, nparts))
         line["variants"]["learned_%d" % m] = learned_variant(hec, torch, m)
         if args.cfg4:
             line["variants"]["learned_200"] = learned_variant(hec, torch, 200)
@@ -351,39 +363,55 @@ def main():
         dist.destroy_process_group()
 
 
-def variants(hec, torch, Ad, L, U, bd, HA0, n, nnzL, nnzU, hbm):
-    """Time-to-1e-8 of the plain FP64 form next to the mixed forms, and L+U sweep bandwidth."""
+def variants(hec, torch, Ad, L, U, bd, HA0, n, nnzL, nnzU, hbm, part):
+    """Time-to-1e-8 of the plain FP64 form next to the mixed forms, and L+U sweep bandwidth, with
+    the global and the x-pencil partitioned single-RHS sweep schedules."""
     out = {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for vdt in ["f64", "f32", "bf16"]:
-        s = hec.IluSolver(L, U, A=Ad, vdt=vdt, max_nrhs=16)
+
+    def timed_solve(s):
         s.solve(bd, restart=RESTART, rtol=RTOL, max_iters=5000)
         torch.cuda.synchronize()
         e0.record()
         x, info = s.solve(bd, restart=RESTART, rtol=RTOL, max_iters=5000)
         e1.record()
         torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / 1000.0
+        return e0.elapsed_time(e1) / 1000.0, info
+
+    def timed_apply(s, r, reps=10):
+        for _ in range(3):
+            s.apply(r)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            s.apply(r)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1000.0 / reps
+
+    for vdt in ["f64", "f32", "bf16"]:
+        s = hec.IluSolver(L, U, A=Ad, vdt=vdt, max_nrhs=16)
+        t, info = timed_solve(s)
         sv = {"f64": 8, "f32": 4, "bf16": 2}[vdt]
         gbs = {}
         for k in (1, 16):
             r = torch.randn(n, k, dtype=torch.float64, device=bd.device) if k > 1 else bd
-            for _ in range(3):
-                s.apply(r)
-            torch.cuda.synchronize()
-            reps = 10
-            e0.record()
-            for _ in range(reps):
-                s.apply(r)
-            e1.record()
-            torch.cuda.synchronize()
-            ta = e0.elapsed_time(e1) / 1000.0 / reps
+            ta = timed_apply(s, r)
             B = sweep_bytes(nnzL, n, k, sv) + sweep_bytes(nnzU, n, k, sv)
             gbs["nrhs%d" % k] = {"lu_us": ta * 1e6, "lu_gbs": B / ta / 1e9, "frac_hbm": B / ta / 1e9 / hbm,
                                  "rows_per_s": n * k / ta}
+        # the same factors with the partitioned single-RHS schedule
+        s.partition(part[0], part[1], threads=PART_THREADS)
+        tp, infop = timed_solve(s)
+        ta = timed_apply(s, bd)
+        B = sweep_bytes(nnzL, n, 1, sv) + sweep_bytes(nnzU, n, 1, sv)
+        gbs["nrhs1_partitioned"] = {"lu_us": ta * 1e6, "lu_gbs": B / ta / 1e9, "frac_hbm": B / ta / 1e9 / hbm,
+                                    "rows_per_s": n / ta}
         out[vdt] = {"time_to_1e-8_s": t, "iterations": info["iterations"], "converged": info["converged"],
-                    "true_rel_residual": info["rel_residual"], "sweeps": gbs, "levels_L": s.lvL.nlev,
-                    "levels_U": s.lvU.nlev}
+                    "true_rel_residual": info["rel_residual"],
+                    "partitioned": {"time_to_1e-8_s": tp, "iterations": infop["iterations"],
+                                    "converged": infop["converged"], "true_rel_residual": infop["rel_residual"]},
+                    "sweeps": gbs, "levels_L": s.lvL.nlev, "levels_U": s.lvU.nlev}
     out.update(batched_variants(hec, torch, Ad, L, U, n, hbm))
     return out
 
@@ -421,6 +449,18 @@ def learned_variant(hec, torch, m, seed=0, crop=32, crops=125, epochs=8, log=Non
             res[name]["stage"] = st.stats()
     res["n"] = m ** 3
     return res
+
+
+PART_THREADS = 1024
+
+
+def sweep_partition(torch, m, device):
+    """x-pencils for the partitioned single-RHS sweep: the y-z plane cut into 12 x 12 boxes (144
+    parts, one resident 1024-thread block each), so a dependency chain crosses a part boundary at
+    most 22 times and every other step stays in one SM's shared memory."""
+    from paper_1606_00541_gb300 import synth
+    part, nparts = synth.grid_boxes(m, (1, 12, 12))
+    return torch.as_tensor(part, device=device), nparts
 
 
 def ras_cuts(m):

@@ -191,7 +191,8 @@ hec_status sptrsv_upper(const sptrsv_plan* p, int nrhs, const double* b, int ldb
  * is then a plain load, and only dependencies on other parts wait point to point through L2.
  * part: device int[n], the part of each ORIGINAL row (compact regions of the grid work best; the
  * paper partitions with METIS), or NULL for contiguous ranges of the original row index.
- * threads: 128 or 256 (0 = 256) per block.  Applies to single-right-hand-side sweeps of this
+ * threads: 128, 256, 512 or 1024 (0 = 256) per block; the part's level is worked by all the
+ * block's warps, so large parts want 1024.  Applies to single-right-hand-side sweeps of this
  * plan (sptrsv_lower / sptrsv_upper / ilu_apply with nrhs = 1); nparts = 0 removes it.  The plan
  * keeps its own copy of the factor in the partitioned order.  Synchronizes `stream`. */
 hec_status sptrsv_plan_partition(sptrsv_plan* p, const int* part, int nparts, int threads,

@@ -550,7 +550,7 @@ struct DepBatchP {
 };
 
 template <typename VT, typename XT, int WMAX>
-__global__ void __launch_bounds__(256) k_sweep_part(PartParams p) {
+__global__ void __launch_bounds__(1024, 1) k_sweep_part(PartParams p) {
     typedef typename Acc<XT>::T AT;
     typedef Word<XT> W;
     typedef typename W::T WT;
@@ -1194,8 +1194,8 @@ HEC_API hec_status sptrsv_plan_partition(sptrsv_plan* p, const int* part, int np
         return HEC_OK;
     }
     if (threads == 0) threads = 256;
-    if (nparts < 1 || (threads != 128 && threads != 256) || p->T->n == 0)
-        return set_error(HEC_ERR_INVALID_ARG, "sptrsv_plan_partition: need nparts >= 1, threads 128 or 256");
+    if (nparts < 1 || (threads != 128 && threads != 256 && threads != 512 && threads != 1024) || p->T->n == 0)
+        return set_error(HEC_ERR_INVALID_ARG, "sptrsv_plan_partition: need nparts >= 1, threads 128, 256, 512 or 1024");
     const int cap0 = part_capacity(p, threads, 0);
     if (nparts > cap0)
         return set_error(HEC_ERR_INVALID_ARG, "sptrsv_plan_partition: " + std::to_string(nparts) +

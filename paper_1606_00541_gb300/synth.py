@@ -151,6 +151,16 @@ def box_partition(m, cuts):
     return part.astype(np.int32), nc ** 3
 
 
+def grid_boxes(m, nb):
+    """Partition of an m^3 grid into nb = (bx, by, bz) boxes of near-equal extent per axis (box k
+    of an axis covers cells floor(k m / b) .. floor((k+1) m / b) - 1).  (1, 12, 12) gives 144 x-pencils
+    of 128 x 10..11 x 10..11 cells on 128^3.  Returns (part[n] int32, number of boxes)."""
+    n, g, x, y, z = _grid3(m)
+    ids = [(c * b) // m for c, b in zip((x, y, z), nb)]
+    part = ids[0] + nb[0] * (ids[1] + nb[1] * ids[2])
+    return part.astype(np.int32), int(nb[0] * nb[1] * nb[2])
+
+
 def random_lower(n, density, seed, unit_diag=False, uplo=0, dominance=None):
     """Random sparse triangular matrix for property tests: each strictly-triangular entry is
     present with probability ``density``; off-diagonal values ~ U[-1, 1]; the diagonal is

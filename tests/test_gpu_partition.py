@@ -55,7 +55,8 @@ def plans(hec, T, uplo, vdt="f64"):
 @pytest.mark.parametrize("kind", ["5pt", "fv7", "fv7_ilu1", "27pt_ilut", "rand"])
 @pytest.mark.parametrize("scheme", ["contiguous", "box", "scattered", "single"])
 @pytest.mark.parametrize("uplo", [0, 1])
-def test_partitioned_sweep_fp64_parity(hec, kind, scheme, uplo):
+@pytest.mark.parametrize("threads", [256, 1024])
+def test_partitioned_sweep_fp64_parity(hec, kind, scheme, uplo, threads):
     A, (L, U), box = factors(kind)
     n = len(A[0]) - 1
     T = L if uplo == 0 else U
@@ -63,14 +64,14 @@ def test_partitioned_sweep_fp64_parity(hec, kind, scheme, uplo):
     if scheme == "box" and box is None:
         pytest.skip("no grid partition for this matrix")
     if scheme == "contiguous":
-        hec.sptrsv_plan_partition(p, None, 37)
+        hec.sptrsv_plan_partition(p, None, 37, threads)
     elif scheme == "box":
-        hec.sptrsv_plan_partition(p, dev(box), int(box.max()) + 1)
+        hec.sptrsv_plan_partition(p, dev(box), int(box.max()) + 1, threads)
     elif scheme == "scattered":
         part = np.random.default_rng(7).integers(0, 23, size=n).astype(np.int32)
-        hec.sptrsv_plan_partition(p, dev(part), 23)
+        hec.sptrsv_plan_partition(p, dev(part), 23, threads)
     else:
-        hec.sptrsv_plan_partition(p, None, 1)
+        hec.sptrsv_plan_partition(p, None, 1, threads)
     b = synth.uniform_vector(n, 12)
     x = (hec.sptrsv_lower if uplo == 0 else hec.sptrsv_upper)(p, dev(b)).cpu().numpy()
     ref = (oracle.lower_solve if uplo == 0 else oracle.upper_solve)(T, b)
