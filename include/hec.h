@@ -163,6 +163,12 @@ typedef struct {
                                   0 disables it, r + 1 selects row r */
     int backoff_ns;         /* nanoseconds a warp sleeps between polls of an unpublished
                                dependency (0 = poll continuously) */
+    int lanes_per_row;      /* lanes sharing a row in single-right-hand-side sweeps: 1, 2, 4 or 8;
+                               0 = by row length (1 while the slab is at most 8 wide and the tail
+                               holds few entries besides the diagonals, else 2 / 4 / 8 for slabs up
+                               to 6 / 12 / wider).  Several lanes poll all of a long row's
+                               dependencies in one wait and add their partial sums with an xor
+                               butterfly (a different summation order from one lane). */
 } hec_tune;
 
 /* A solve plan for one triangular factor: its HEC form and level analysis (both borrowed; they

@@ -125,6 +125,7 @@ struct sptrsv_plan {
     int2* chunks[5] = {};      // level-aligned chunk tables for 32, 16, 8, 4, 2 rows per warp step
     int nchunks[5] = {};
     void* dinv = nullptr;      // reciprocal diagonal in the work type (NULL: the kernel divides)
+    int lpr1 = 1;              // lanes per row of single-right-hand-side sweeps (1, 2, 4 or 8)
 };
 
 struct ilu_precond {

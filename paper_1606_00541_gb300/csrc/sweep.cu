@@ -252,6 +252,104 @@ __global__ void __launch_bounds__(256) k_sweep(SweepParams p) {
     }
 }
 
+// ---- several lanes per row (one right-hand side, long rows) --------------------------------
+// LPR lanes share a row: lane `sub` of the group takes slab slots sub, sub + LPR, ... and tail
+// entries sub, sub + LPR, ..., so every dependency of the row is polled in the same warp-wide
+// wait (a row with w slab slots and t tail entries needs one wait for w <= LPR*SPL and
+// t <= LPR*TB, where the one-lane kernel would wait once per slot beyond its register batch);
+// wider slabs and longer tails take further rounds.
+// The partial sums are combined by an xor butterfly, which gives every lane of the group the
+// same bits; the fixed pairing makes the result deterministic (it differs from the one-lane
+// kernel only in summation order).
+template <typename VT, typename XT, int LPR, int SPL, int TB>
+__global__ void __launch_bounds__(256) k_sweep_lpr(SweepParams p) {
+    typedef typename Acc<XT>::T AT;
+    constexpr int NS = SPL + TB;
+    const int lane = threadIdx.x & 31;
+    const int rsub = lane / LPR, sub = lane % LPR;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const VT* __restrict__ ev = (const VT*)p.ell_val;
+    const VT* __restrict__ tv = (const VT*)p.tval;
+    XT* xp = (XT*)p.xp;
+    for (int c = gw; c < p.nchunks; c += nw) {
+        const int2 ch = __ldg(p.chunks + c);
+        const int r = ch.x + rsub;
+        const bool act = rsub < ch.y;
+        AT acc = AT(0), diag = AT(1);
+        int t0 = 0, tl = 0, sr = -1;
+        if (act) {
+            t0 = __ldg(p.tptr + r);
+            const int t1 = __ldg(p.tptr + r + 1) - 1;
+            tl = t1 - t0;
+            if (sub == 0) {
+                const int gr = p.gather ? __ldg(p.gather + r) : r;
+                acc = (AT)__ldg(p.b + (long)gr * p.ldb);
+                diag = p.dinv ? (AT)__ldg((const XT*)p.dinv + r) : ldv<VT, AT>(tv + t1);
+                sr = p.scatter ? __ldg(p.scatter + r) : r;
+            }
+        }
+        // slab slots of this lane, then its first tail entries, all polled in one wait
+        DepBatch<XT, AT, NS> dep;
+        dep.clear(xp);
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+            const int k = sub + j * LPR;
+            if (act && k < p.w) {
+                const long s = (long)k * p.ld + r;
+                const int cc = __ldg(p.ell_col + s);
+                if (cc >= 0) dep.set(j, xp + cc, ldv<VT, AT>(ev + s));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < TB; ++j) {
+            const int t = sub + j * LPR;
+            if (act && t < tl) dep.set(SPL + j, xp + __ldg(p.tcol + t0 + t), ldv<VT, AT>(tv + t0 + t));
+        }
+        dep.poll();
+        dep.wait(p.status, p.budget, p.backoff_ns);
+        acc = dep.accumulate(acc);
+        // wider slabs: further rounds of LPR * SPL slots (p.w is the same for every lane)
+        for (int kb = LPR * SPL; kb < p.w; kb += LPR * SPL) {
+            DepBatch<XT, AT, SPL> more;
+            more.clear(xp);
+#pragma unroll
+            for (int j = 0; j < SPL; ++j) {
+                const int k = kb + sub + j * LPR;
+                if (act && k < p.w) {
+                    const long s = (long)k * p.ld + r;
+                    const int cc = __ldg(p.ell_col + s);
+                    if (cc >= 0) more.set(j, xp + cc, ldv<VT, AT>(ev + s));
+                }
+            }
+            more.poll();
+            more.wait(p.status, p.budget, p.backoff_ns);
+            acc = more.accumulate(acc);
+        }
+        // longer tails: further rounds of LPR * TB entries (warp-uniform trip count)
+        const int tmax = __reduce_max_sync(kFull, tl);
+        for (int tb = LPR * TB; tb < tmax; tb += LPR * TB) {
+            DepBatch<XT, AT, TB> more;
+            more.clear(xp);
+#pragma unroll
+            for (int j = 0; j < TB; ++j) {
+                const int t = tb + sub + j * LPR;
+                if (act && t < tl) more.set(j, xp + __ldg(p.tcol + t0 + t), ldv<VT, AT>(tv + t0 + t));
+            }
+            more.poll();
+            more.wait(p.status, p.budget, p.backoff_ns);
+            acc = more.accumulate(acc);
+        }
+#pragma unroll
+        for (int off = LPR / 2; off >= 1; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+        if (act && sub == 0) {
+            const AT xr = p.dinv ? acc * diag : acc / diag;
+            if (r != p.skip_row) publish_x(xp + r, (XT)xr);
+            if (sr >= 0) p.x[(long)sr * p.ldx] = (double)xr;
+        }
+    }
+}
+
 // ---- several right-hand sides per lane ------------------------------------------------------
 // For nrhs > 1 a lane carries G consecutive right-hand sides of one row (G = 4 for FP32 work,
 // 2 for FP64) and moves them with one 16-byte (or 8-byte) relaxed vector access; LPR = KP / G
@@ -712,6 +810,35 @@ hec_status launch_sweep_vec(const sptrsv_plan* pl, SweepParams& sp, cudaStream_t
     return HEC_OK;
 }
 
+template <typename VT, typename XT, int LPR>
+hec_status launch_sweep_lpr(const sptrsv_plan* pl, SweepParams& sp, cudaStream_t s) {
+    const void* k = (const void*)k_sweep_lpr<VT, XT, LPR, 3, 2>;
+    const int threads = pl->threads;
+    int per_sm = occupancy(k, threads);
+    if (per_sm <= 0) return set_error(HEC_ERR_CUDA, "sweep kernel cannot be resident");
+    if (pl->blocks > 0) per_sm = std::min(per_sm, pl->blocks);
+    constexpr int idx = LPR == 2 ? 1 : LPR == 4 ? 2 : 3;
+    if (!pl->chunks[idx]) return set_error(HEC_ERR_INVALID_ARG, "sweep: no chunk table for the plan's lanes per row");
+    sp.chunks = pl->chunks[idx];
+    sp.nchunks = pl->nchunks[idx];
+    const long want = ((long)sp.nchunks + threads / 32 - 1) / (threads / 32);
+    const int blocks = (int)std::max(1L, std::min((long)per_sm * num_sms(), want));
+    const long count = sp.n;
+    const int fb = (int)std::min(4096L, std::max(1L, (count + 255) / 256));
+    {
+        ProfScope ps_(s, PROF_FILL);
+        k_fill_sentinel<XT><<<fb, 256, 0, s>>>((XT*)sp.xp, count);
+    }
+    HEC_LAUNCHED();
+    void* args[] = {&sp};
+    void* tok = nullptr;
+    profile_begin(s, &tok);
+    HEC_CUDA(cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(threads), args, 0, s));
+    profile_end(s, tok);
+    count_launch();
+    return HEC_OK;
+}
+
 // one right-hand side: lane per row; more: G right-hand sides per lane, LPR lanes per row
 template <typename VT, typename XT, int WMAX>
 hec_status dispatch_k(const sptrsv_plan* pl, SweepParams& sp, cudaStream_t s) {
@@ -726,6 +853,11 @@ hec_status dispatch_k(const sptrsv_plan* pl, SweepParams& sp, cudaStream_t s) {
 // slab slots held in registers: 4 covers the 5- and 7-point ILU(0) factors, 8 the wider ones
 template <typename VT, typename XT>
 hec_status dispatch_w(const sptrsv_plan* pl, SweepParams& sp, cudaStream_t s) {
+    if (sp.K <= 1 && pl->lpr1 > 1) {  // long rows: several lanes per row (one wait per row)
+        if (pl->lpr1 == 2) return launch_sweep_lpr<VT, XT, 2>(pl, sp, s);
+        if (pl->lpr1 == 4) return launch_sweep_lpr<VT, XT, 4>(pl, sp, s);
+        return launch_sweep_lpr<VT, XT, 8>(pl, sp, s);
+    }
     if (sp.w <= 4) return dispatch_k<VT, XT, 4>(pl, sp, s);
     return dispatch_k<VT, XT, 8>(pl, sp, s);
 }
@@ -781,6 +913,7 @@ hec_status build_chunks(sptrsv_plan* p) {
     cudaStream_t s = 0;
     unsigned needed = 0;  // only the lane layouts this plan can be called with
     for (int k = 1; k <= p->max_nrhs; ++k) needed |= 1u << log2i(sweep_lpr(k, p->T->vdt));
+    needed |= 1u << log2i(p->lpr1);
     for (int i = 0; i < 5 && st == HEC_OK; ++i) {
         const int rpw = 32 >> i;
         if (!(needed & (1u << i))) continue;
@@ -1171,6 +1304,17 @@ HEC_API hec_status sptrsv_plan_create(const hec_matrix* tri, const hec_levels* l
         if (tune->debug_unpublished_row > 0) p->skip_row = tune->debug_unpublished_row - 1;
         if (tune->backoff_ns > 0) p->backoff_ns = tune->backoff_ns;
     }
+    // single-RHS lanes per row by row length: the one-lane kernel polls up to 8 slab slots and 4
+    // tail entries per wait and waits again for every further slot; several lanes per row poll
+    // 3 slab slots and 2 tail entries each, all in one wait
+    const long long over = tri->tail_nnz - (long long)tri->n;  // tail entries besides the diagonals
+    if (tri->w <= 8 && over * 2 <= (long long)tri->n) p->lpr1 = 1;
+    else p->lpr1 = tri->w <= 6 ? 2 : tri->w <= 12 ? 4 : 8;
+    if (tune && tune->lanes_per_row) p->lpr1 = tune->lanes_per_row;
+    if (p->lpr1 != 1 && p->lpr1 != 2 && p->lpr1 != 4 && p->lpr1 != 8) {
+        delete p;
+        return set_error(HEC_ERR_INVALID_ARG, "sptrsv_plan_create: lanes_per_row must be 0, 1, 2, 4 or 8");
+    }
     if (p->threads % 32 || p->threads < 32 || p->threads > 256) {
         delete p;
         return set_error(HEC_ERR_INVALID_ARG, "sptrsv_plan_create: block_threads must be a multiple of 32 in [32, 256]");
@@ -1292,7 +1436,7 @@ HEC_API hec_status sptrsv_autotune(sptrsv_plan* p, int nrhs, hec_tune* out, void
         if (it != g_tune_cache.end()) {
             p->threads = it->second.first;
             p->blocks = it->second.second;
-            if (out) { *out = hec_tune{}; out->block_threads = p->threads; out->blocks_per_sm = p->blocks; }
+            if (out) { *out = hec_tune{}; out->block_threads = p->threads; out->blocks_per_sm = p->blocks; out->lanes_per_row = p->lpr1; }
             return HEC_OK;
         }
     }
@@ -1338,7 +1482,7 @@ HEC_API hec_status sptrsv_autotune(sptrsv_plan* p, int nrhs, hec_tune* out, void
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_tune_cache[key] = {bt, bb};
     }
-    if (out) { *out = hec_tune{}; out->block_threads = bt; out->blocks_per_sm = bb; }
+    if (out) { *out = hec_tune{}; out->block_threads = bt; out->blocks_per_sm = bb; out->lanes_per_row = p->lpr1; }
     return hec_sync_status(p, stream);
 }
 
