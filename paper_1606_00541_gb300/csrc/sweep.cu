@@ -221,18 +221,22 @@ __global__ void __launch_bounds__(256) k_sweep(SweepParams p) {
         slab.poll();
         slab.wait(p.status, p.budget, p.backoff_ns);
         acc = slab.accumulate(acc);
-        // wider slabs: the remaining slots one at a time (same order)
-        for (int k = WMAX; k < p.w; ++k) {
-            DepBatch<XT, AT, 1> one;
-            one.clear(xp);
-            if (act) {
-                const long s = (long)k * p.ld + r;
-                const int cc = __ldg(p.ell_col + s);
-                if (cc >= 0) one.set(0, xp + (long)cc * K + q, ldv<VT, AT>(ev + s));
+        // wider slabs: the remaining slots kTailBatch at a time (same order)
+        for (int kb = WMAX; kb < p.w; kb += kTailBatch) {
+            DepBatch<XT, AT, kTailBatch> more;
+            more.clear(xp);
+#pragma unroll
+            for (int j = 0; j < kTailBatch; ++j) {
+                const int k = kb + j;
+                if (act && k < p.w) {
+                    const long s = (long)k * p.ld + r;
+                    const int cc = __ldg(p.ell_col + s);
+                    if (cc >= 0) more.set(j, xp + (long)cc * K + q, ldv<VT, AT>(ev + s));
+                }
             }
-            one.poll();
-            one.wait(p.status, p.budget, p.backoff_ns);
-            acc = one.accumulate(acc);
+            more.poll();
+            more.wait(p.status, p.budget, p.backoff_ns);
+            acc = more.accumulate(acc);
         }
         // tail overflow entries in ascending new column, kTailBatch at a time (warp-uniform count)
         for (int tb = 0; tb < tmax; tb += kTailBatch) {
@@ -498,17 +502,22 @@ __global__ void __launch_bounds__(256) k_sweep_vec(SweepParams p) {
         slab.poll();
         slab.wait(p.status, p.budget, p.backoff_ns);
         slab.accumulate(acc);
-        for (int k = WMAX; k < p.w; ++k) {
-            DepBatchV<XT, AT, 1, G> one;
-            one.clear(xp);
-            if (act) {
-                const long s = (long)k * p.ld + r;
-                const int cc = __ldg(p.ell_col + s);
-                if (cc >= 0) one.set(0, xp + (long)cc * KS + q0, ldv<VT, AT>(ev + s));
+        // wider slabs: the remaining slots kTailBatch at a time, in slot order
+        for (int kb = WMAX; kb < p.w; kb += kTailBatch) {
+            DepBatchV<XT, AT, kTailBatch, G> more;
+            more.clear(xp);
+#pragma unroll
+            for (int j = 0; j < kTailBatch; ++j) {
+                const int k = kb + j;
+                if (act && k < p.w) {
+                    const long s = (long)k * p.ld + r;
+                    const int cc = __ldg(p.ell_col + s);
+                    if (cc >= 0) more.set(j, xp + (long)cc * KS + q0, ldv<VT, AT>(ev + s));
+                }
             }
-            one.poll();
-            one.wait(p.status, p.budget, p.backoff_ns);
-            one.accumulate(acc);
+            more.poll();
+            more.wait(p.status, p.budget, p.backoff_ns);
+            more.accumulate(acc);
         }
         const int tmax = __reduce_max_sync(kFull, tl);
         for (int tb = 0; tb < tmax; tb += kTailBatch) {
@@ -692,17 +701,21 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_part(PartParams p) {
         slab.poll();
         slab.wait(p.status, p.budget);
         acc = slab.accumulate(acc);
-        for (int k = WMAX; k < p.w; ++k) {
-            DepBatchP<XT, AT, 1> one;
-            one.clear();
-            if (act) {
-                const long s = (long)k * p.ld + r;
-                const int cc = __ldg(p.ell_col + s);
-                if (cc >= 0) one.set(0, xp, sxp, cc, lo, hi, ldv<VT, AT>(ev + s));
+        for (int kb = WMAX; kb < p.w; kb += kTailBatch) {  // wider slabs, kTailBatch slots at a time
+            DepBatchP<XT, AT, kTailBatch> more;
+            more.clear();
+#pragma unroll
+            for (int j = 0; j < kTailBatch; ++j) {
+                const int k = kb + j;
+                if (act && k < p.w) {
+                    const long s = (long)k * p.ld + r;
+                    const int cc = __ldg(p.ell_col + s);
+                    if (cc >= 0) more.set(j, xp, sxp, cc, lo, hi, ldv<VT, AT>(ev + s));
+                }
             }
-            one.poll();
-            one.wait(p.status, p.budget);
-            acc = one.accumulate(acc);
+            more.poll();
+            more.wait(p.status, p.budget);
+            acc = more.accumulate(acc);
         }
         for (int tb = 0; tb < tmax; tb += kTailBatch) {
             DepBatchP<XT, AT, kTailBatch> tail;
