@@ -413,6 +413,7 @@ def variants(hec, torch, Ad, L, U, bd, HA0, n, nnzL, nnzU, hbm, part):
                                     "converged": infop["converged"], "true_rel_residual": infop["rel_residual"]},
                     "sweeps": gbs, "levels_L": s.lvL.nlev, "levels_U": s.lvU.nlev}
     out.update(batched_variants(hec, torch, Ad, L, U, n, hbm))
+    out["stencil27_ilu0_100"] = long_row_variant(hec, torch, hbm, Ad[0].device)
     return out
 
 
@@ -467,6 +468,50 @@ def ras_cuts(m):
     """Per-axis box cuts: [25, 39, 25, 39] on 128 (64 boxes of 25^3 .. 39^3 owned rows)."""
     a, b = m * 25 // 128, m * 39 // 128
     return [a, b, a, m - 2 * a - b]
+
+
+def long_row_variant(hec, torch, hbm, device, m=100):
+    """Long rows: the 27-point jittered stencil on 100^3 with its GPU ILU(0) (13 strictly lower
+    entries per interior row), single-RHS L+U apply with one lane per row against the lanes per
+    row the plan picks from the row length, and FGMRES(30) to 1e-8 with FP32 factor values."""
+    from paper_1606_00541_gb300 import synth
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    A = [torch.as_tensor(a, device=device) for a in synth.stencil27_jitter(m, seed=0)]
+    n = m ** 3
+    Lh, Uh = hec.ilu_factor(*A, k=0)
+    L, U = Lh.tensors(), Uh.tensors()
+    nnzL, nnzU = L[1].numel(), U[1].numel()
+    b = hec.spmv(hec.hec_from_csr(*A), torch.as_tensor(synth.uniform_vector(n, 600), device=device))
+    out = {"n": n, "nnz_A": int(A[1].numel()), "nnz_L": nnzL, "nnz_U": nnzU}
+    for vdt, sv in (("f64", 8), ("f32", 4)):
+        res = {}
+        for lpr in (1, 0):
+            s = hec.IluSolver(L, U, A=A, vdt=vdt, lanes_per_row=lpr)
+            for _ in range(3):
+                s.apply(b)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(10):
+                s.apply(b)
+            e1.record()
+            torch.cuda.synchronize()
+            ta = e0.elapsed_time(e1) / 1000.0 / 10
+            B = sweep_bytes(nnzL, n, 1, sv) + sweep_bytes(nnzU, n, 1, sv)
+            key = "one_lane" if lpr == 1 else "lanes_%d" % hec.sptrsv_autotune(s.pL, 1)["lanes_per_row"]
+            res[key] = {"lu_us": ta * 1e6, "lu_gbs": B / ta / 1e9, "frac_hbm": B / ta / 1e9 / hbm}
+            if lpr == 0:
+                s.solve(b, restart=RESTART, rtol=RTOL, max_iters=5000)
+                torch.cuda.synchronize()
+                e0.record()
+                _, info = s.solve(b, restart=RESTART, rtol=RTOL, max_iters=5000)
+                e1.record()
+                torch.cuda.synchronize()
+                res["time_to_1e-8_s"] = e0.elapsed_time(e1) / 1000.0
+                res["iterations"] = info["iterations"]
+                res["converged"] = info["converged"]
+                res["levels_L"], res["levels_U"] = s.lvL.nlev, s.lvU.nlev
+        out[vdt] = res
+    return out
 
 
 def batched_variants(hec, torch, Ad, L, U, n, hbm):
