@@ -431,9 +431,10 @@ def learned_variant(hec, torch, m, seed=0, crop=32, crops=125, epochs=8, log=Non
     Lh, Uh = hec.ilu_factor(*Ad, k=0)
     s = hec.IluSolver(Lh.tensors(), Uh.tensors(), A=Ad, vdt="f32")
     b = hec.spmv(s.A, torch.as_tensor(synth.uniform_vector(m ** 3, seed + 1), device="cuda"))
+    schedule = pick_schedule(hec, torch, s, m, b)  # the faster single-RHS schedule, for both forms
     stage = hec.Stage(net, s.A, (m, m, m), torch.as_tensor(lnk, device="cuda"), rho=0.99)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    res = {"train": tinfo}
+    res = {"train": tinfo, "sweep_schedule": schedule}
     for name, st in (("plain", None), ("learned", stage)):
         hec.fgmres_solve(s.A, s.M, b, stage=st, restart=RESTART, rtol=RTOL, max_iters=5000)  # warm
         if st is not None:
@@ -455,12 +456,37 @@ def learned_variant(hec, torch, m, seed=0, crop=32, crops=125, epochs=8, log=Non
 PART_THREADS = 1024
 
 
+def pick_schedule(hec, torch, s, m, b, reps=5):
+    """Times the ILU apply with the global sweep and with the x-pencil partition and keeps the
+    faster one on the solver; returns a description with both times."""
+    def t_apply():
+        s.apply(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            s.apply(b)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+    tg = t_apply()
+    part_d, nparts = sweep_partition(torch, m, b.device)
+    try:
+        s.partition(part_d, nparts, threads=PART_THREADS)
+    except hec.HecError as e:
+        return "global (partition refused: %s)" % e
+    tp = t_apply()
+    if tp < tg:
+        return "x-pencil partitioned, %d parts (L+U %.0f us; global %.0f us)" % (nparts, tp * 1e6, tg * 1e6)
+    s.partition(None, 0)
+    return "global (L+U %.0f us; partitioned %.0f us)" % (tg * 1e6, tp * 1e6)
+
+
 def sweep_partition(torch, m, device):
     """x-pencils for the partitioned single-RHS sweep: the y-z plane cut into 12 x 12 boxes (144
     parts, one resident 1024-thread block each), so a dependency chain crosses a part boundary at
-    most 22 times and every other step stays in one SM's shared memory."""
+    most 22 times and every other step stays in one SM's shared memory.  Grids above 160^3 take
+    8 x 19 pencils (152 parts) so that a part's FP32 solution still fits in shared memory."""
     from paper_1606_00541_gb300 import synth
-    part, nparts = synth.grid_boxes(m, (1, 12, 12))
+    part, nparts = synth.grid_boxes(m, (1, 12, 12) if m <= 160 else (1, 8, 19))
     return torch.as_tensor(part, device=device), nparts
 
 

@@ -672,8 +672,12 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_part(PartParams p) {
     const VT* __restrict__ ev = (const VT*)p.ell_val;
     const VT* __restrict__ tv = (const VT*)p.tval;
     XT* xp = (XT*)p.xp;
+    // the warp's next chunk entry is fetched while it works on the current one, so the chain of
+    // dependent loads that starts a chunk (entry -> row data -> b) is one link shorter
+    int2 ch_next = c0 + warp < c1 ? __ldg(p.chunks + c0 + warp) : make_int2(0, 0);
     for (int c = c0 + warp; c < c1; c += nwarps) {
-        const int2 ch = __ldg(p.chunks + c);
+        const int2 ch = ch_next;
+        if (c + nwarps < c1) ch_next = __ldg(p.chunks + c + nwarps);
         const int r = ch.x + lane;
         const bool act = lane < ch.y;
         AT acc = AT(0), diag = AT(1);
