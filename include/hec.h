@@ -359,6 +359,20 @@ hec_status csr_triangle(int n, const int* rowptr, const int* col, const double* 
 hec_status ilu_factor(int n, const int* rowptr, const int* col, const double* val, int k,
                       hec_csr** L, hec_csr** U, void* stream);
 
+/* ILUT(p, tol) (Sec. 3 lists ILUT among the preconditioners; the dual-threshold rule is Saad's):
+ * for row i, tau_i = tol * ||a_i||_2 (squares summed in row order); the row's entries k < i,
+ * including fill, are eliminated in ascending column order: w_k <- w_k / u_kk, dropped when
+ * |w_k| < tau_i, else w_j <- w_j - (w_k * u_kj) for the entries j > k of U row k.  Then entries
+ * with w_j = 0 or |w_j| < tau_i are dropped and the p largest magnitudes kept in the strict lower
+ * and in the strict upper part (ties to the smaller column); the diagonal is always kept (a
+ * missing diagonal gets a structural zero slot).  Every operation is rounded separately (no
+ * fused multiply-add), in this order.  Outputs L (unit lower, the 1.0 diagonal stored last in its
+ * row) and U (upper, diagonal first), columns ascending.  A's rows must be sorted ascending.
+ * Errors: ZERO_PIVOT; OUT_OF_BOUNDS when a row's working fill exceeds 9000 entries; TIMEOUT if a
+ * dependency wait runs out.  Synchronizes `stream`. */
+hec_status ilut_factor(int n, const int* rowptr, const int* col, const double* val, int p,
+                       double tol, hec_csr** L, hec_csr** U, void* stream);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Restricted Additive Schwarz setup (Sec. 3; Eq. 4: the subdomain problems as one            */
 /* block-diagonal system)                                                                     */

@@ -405,6 +405,18 @@ def ilu_factor(rowptr, col, val, k=0, stream=None):
     return Csr(L.value), Csr(U.value)
 
 
+_ilut_factor = _sig("ilut_factor", _i, _vp, _vp, _vp, _i, _d, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp)
+
+
+def ilut_factor(rowptr, col, val, p=10, tol=1e-3, stream=None):
+    """ILUT(p, tol) of a device CSR matrix (rows ascending) on the GPU; returns (L, U) handles."""
+    n = rowptr.numel() - 1
+    L, U = _vp(), _vp()
+    _check(_ilut_factor(n, _ptr(rowptr), _ptr(col), _ptr(val), int(p), float(tol), ctypes.byref(L), ctypes.byref(U),
+                        _stream(stream)), "ilut_factor")
+    return Csr(L.value), Csr(U.value)
+
+
 _csr_triangle = _sig("csr_triangle", _i, _vp, _vp, _vp, _i, _i, ctypes.POINTER(_vp), _vp)
 
 
