@@ -414,6 +414,7 @@ def variants(hec, torch, Ad, L, U, bd, HA0, n, nnzL, nnzU, hbm, part):
                     "sweeps": gbs, "levels_L": s.lvL.nlev, "levels_U": s.lvU.nlev}
     out.update(batched_variants(hec, torch, Ad, L, U, n, hbm))
     out["stencil27_ilu0_100"] = long_row_variant(hec, torch, hbm, Ad[0].device)
+    out["stencil27_ilut_100"] = long_row_variant(hec, torch, hbm, Ad[0].device, ilut=(10, 1e-3))
     return out
 
 
@@ -496,19 +497,25 @@ def ras_cuts(m):
     return [a, b, a, m - 2 * a - b]
 
 
-def long_row_variant(hec, torch, hbm, device, m=100):
-    """Long rows: the 27-point jittered stencil on 100^3 with its GPU ILU(0) (13 strictly lower
-    entries per interior row), single-RHS L+U apply with one lane per row against the lanes per
-    row the plan picks from the row length, and FGMRES(30) to 1e-8 with FP32 factor values."""
+def long_row_variant(hec, torch, hbm, device, m=100, ilut=None):
+    """Long rows: the 27-point jittered stencil on 100^3 (a_ii = 1.05 sum |a_ij|, +-30 % jitter)
+    with its GPU ILU(0) (13 strictly lower entries per interior row) or GPU ILUT(p, tol);
+    single-RHS L+U apply with one lane per row against the lanes per row the plan picks from the
+    row length, 16-RHS L+U, and FGMRES(30) to 1e-8 with FP32 and FP64 factor values."""
     from paper_1606_00541_gb300 import synth
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     A = [torch.as_tensor(a, device=device) for a in synth.stencil27_jitter(m, seed=0)]
     n = m ** 3
-    Lh, Uh = hec.ilu_factor(*A, k=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Lh, Uh = hec.ilut_factor(*A, p=ilut[0], tol=ilut[1]) if ilut else hec.ilu_factor(*A, k=0)
+    torch.cuda.synchronize()
+    factor_s = time.perf_counter() - t0
     L, U = Lh.tensors(), Uh.tensors()
     nnzL, nnzU = L[1].numel(), U[1].numel()
     b = hec.spmv(hec.hec_from_csr(*A), torch.as_tensor(synth.uniform_vector(n, 600), device=device))
-    out = {"n": n, "nnz_A": int(A[1].numel()), "nnz_L": nnzL, "nnz_U": nnzU}
+    out = {"factorization": "ILUT(%d, %g)" % ilut if ilut else "ILU(0)", "factor_s": factor_s, "n": n,
+           "nnz_A": int(A[1].numel()), "nnz_L": nnzL, "nnz_U": nnzU}
     for vdt, sv in (("f64", 8), ("f32", 4)):
         res = {}
         for lpr in (1, 0):
@@ -536,6 +543,19 @@ def long_row_variant(hec, torch, hbm, device, m=100):
                 res["iterations"] = info["iterations"]
                 res["converged"] = info["converged"]
                 res["levels_L"], res["levels_U"] = s.lvL.nlev, s.lvU.nlev
+        s16 = hec.IluSolver(L, U, vdt=vdt, max_nrhs=16)
+        r16 = torch.randn(n, 16, dtype=torch.float64, device=device)
+        for _ in range(3):
+            s16.apply(r16)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(5):
+            s16.apply(r16)
+        e1.record()
+        torch.cuda.synchronize()
+        t16 = e0.elapsed_time(e1) / 1000.0 / 5
+        B16 = sweep_bytes(nnzL, n, 16, sv) + sweep_bytes(nnzU, n, 16, sv)
+        res["nrhs16"] = {"lu_us": t16 * 1e6, "lu_gbs": B16 / t16 / 1e9, "frac_hbm": B16 / t16 / 1e9 / hbm}
         out[vdt] = res
     return out
 

@@ -624,13 +624,18 @@ class IluSolver:
 class RasSolver(IluSolver):
     """RAS preconditioner (Sec. 3, Eq. 4): ras_setup on the GPU, ILU(0) of the block-diagonal
     subdomain system, one pair of batched sweeps for all subdomains, restricted write-back.
-    Pass `factors=(L, U)` to use given block-diagonal factors instead of the GPU ILU(0);
-    overlap=0 gives block ILU (block Jacobi with ILU blocks)."""
+    Pass `factors=(L, U)` to use given block-diagonal factors instead of the GPU ILU(0), or
+    `ilut=(p, tol)` for the GPU ILUT of every block; overlap=0 gives block ILU / block ILUT (the
+    paper's BILU and BILUT: block Jacobi with incomplete-factor blocks)."""
 
-    def __init__(self, A, part, nsub, vdt="f32", max_nrhs=1, stream=None, factors=None, overlap=1, **tune):
+    def __init__(self, A, part, nsub, vdt="f32", max_nrhs=1, stream=None, factors=None, overlap=1, ilut=None,
+                 **tune):
         self.R = ras_setup(*A, part, nsub, stream, overlap=overlap)
         self.ext_ptr, self.ext2glob, self.owned, self.A_ext = self.R.tensors(nsub)
-        if factors is None:
+        if factors is None and ilut is not None:
+            Lh, Uh = ilut_factor(*self.A_ext, p=ilut[0], tol=ilut[1], stream=stream)
+            L, U = Lh.tensors(), Uh.tensors()
+        elif factors is None:
             Lh, Uh = ilu_factor(*self.A_ext, k=0, stream=stream)
             L, U = Lh.tensors(), Uh.tensors()
         else:
