@@ -115,6 +115,16 @@ def test_cfg2_ilut_27pt_sweeps_1_and_16_rhs(hec):
                 assert relmax(X[:, q], refs[q]) <= 1e-12
 
 
+def test_cfg2_gpu_ilut_bit_exact_full_size(hec):
+    """GPU ILUT(10, 1e-3) of the 27-point 100^3 matrix equals the oracle's factors bit for bit."""
+    A = synth.stencil27_jitter(100, seed=0)
+    Lo, Uo = oracle.ilut(A, 10, 1e-3)
+    Lh, Uh = hec.ilut_factor(*[dev(a) for a in A], p=10, tol=1e-3)
+    for got, ref in ((Lh.tensors(), Lo), (Uh.tensors(), Uo)):
+        for g, r in zip(got, ref):
+            assert np.array_equal(g.cpu().numpy(), r)
+
+
 def test_cfg3_ras64_16_rhs(hec):
     m = 128
     A = synth.fv7_lognormal(m, sigma=2.0, seed=0)
