@@ -71,15 +71,79 @@ __device__ __forceinline__ int lower_bound(const int* cols, int lo, int hi, int 
 namespace hec {
 namespace {
 
-// publish row i: its U length is the flag later rows wait on (release after the warp's stores)
-__device__ __forceinline__ void ilut_publish(const IlutParams& P, int i, int lane, int nl, int nu1) {
+// publish U row i: its length is the flag later rows wait on (release after the warp's stores)
+__device__ __forceinline__ void ilut_publish(const IlutParams& P, int i, int lane, int nu1) {
     __syncwarp();
     if (lane == 0) {
-        P.llen[i] = nl;
         __threadfence();
         st_release_i32(P.ulen + i, nu1);
     }
     __syncwarp();
+}
+
+// One strict part of a finished row, list positions [b0, b1): the entries with w != 0 and
+// |w| >= tau are the candidates; the p largest magnitudes are kept (ties to the smaller column)
+// and written to out_col / out_val in column order.  The candidates are first compacted, in
+// column order, into the warp's spare buffer; up to 64 of them are ranked with shuffles (two per
+// lane), more by a scan of the compacted list.  Returns the number kept.
+__device__ __forceinline__ int ilut_select(const int* col, const double* val, int b0, int b1, double tau, int p,
+                                           int lane, int* scol, double* sval, int* out_col, double* out_val) {
+    const unsigned lt = (1u << lane) - 1u;
+    int m = 0;
+    for (int bb = b0; bb < b1; bb += 32) {
+        const int b = bb + lane;
+        bool c = false;
+        if (b < b1) {
+            const double v = val[b];
+            c = v != 0.0 && !(fabs(v) < tau);
+        }
+        const unsigned cm = __ballot_sync(kAll, c);
+        if (c) {
+            scol[m + __popc(cm & lt)] = col[b];
+            sval[m + __popc(cm & lt)] = val[b];
+        }
+        m += __popc(cm);
+    }
+    __syncwarp();
+    if (m == 0 || p == 0) return 0;
+    int kept = 0;
+    if (m <= 64) {
+        const bool h0 = lane < m, h1 = lane + 32 < m;
+        const double a0 = h0 ? fabs(sval[lane]) : 0.0, a1 = h1 ? fabs(sval[lane + 32]) : 0.0;
+        int r0 = 0, r1 = 0;  // candidates ahead of this lane's two (larger, or equal with a smaller column)
+        for (int t = 0; t < m; ++t) {
+            const double at = __shfl_sync(kAll, t < 32 ? a0 : a1, t & 31);
+            r0 += (at > a0 || (at == a0 && t < lane)) ? 1 : 0;
+            r1 += (at > a1 || (at == a1 && t < lane + 32)) ? 1 : 0;
+        }
+        const bool k0 = h0 && r0 < p, k1 = h1 && r1 < p;
+        const unsigned m0 = __ballot_sync(kAll, k0), m1 = __ballot_sync(kAll, k1);
+        if (k0) { out_col[__popc(m0 & lt)] = scol[lane]; out_val[__popc(m0 & lt)] = sval[lane]; }
+        if (k1) {
+            out_col[__popc(m0) + __popc(m1 & lt)] = scol[lane + 32];
+            out_val[__popc(m0) + __popc(m1 & lt)] = sval[lane + 32];
+        }
+        kept = __popc(m0) + __popc(m1);
+    } else {
+        for (int eb = 0; eb < m; eb += 32) {
+            const int e = eb + lane;
+            bool k = false;
+            if (e < m) {
+                const double ae = fabs(sval[e]);
+                int rank = 0;
+                for (int t = 0; t < m && rank < p; ++t) {
+                    const double at = fabs(sval[t]);
+                    rank += (at > ae || (at == ae && t < e)) ? 1 : 0;
+                }
+                k = rank < p;
+            }
+            const unsigned km = __ballot_sync(kAll, k);
+            if (k) { out_col[kept + __popc(km & lt)] = scol[e]; out_val[kept + __popc(km & lt)] = sval[e]; }
+            kept += __popc(km);
+        }
+    }
+    __syncwarp();
+    return kept;
 }
 
 // a row that cannot be factored (error recorded): diagonal 1.0 only, so later rows still finish
@@ -88,8 +152,9 @@ __device__ __forceinline__ void ilut_fail(const IlutParams& P, int i, int lane, 
         record(P.status, code);
         P.ucol[(long)i * (P.p + 1)] = i;
         P.uval[(long)i * (P.p + 1)] = 1.0;
+        P.llen[i] = 0;
     }
-    ilut_publish(P, i, lane, 0, 1);
+    ilut_publish(P, i, lane, 1);
 }
 
 __global__ void __launch_bounds__(256) k_ilut(IlutParams P) {
@@ -154,7 +219,14 @@ __global__ void __launch_bounds__(256) k_ilut(IlutParams P) {
             }
             ul = __shfl_sync(kAll, ul, 0);
             if (ul < 0) { failed = HEC_ERR_TIMEOUT; break; }
-            const double wk = __ddiv_rn(val[pos], ldcg_d(P.uval + (long)k * up));  // u_kk is U row k's first entry
+            // U row k's first 32 entries in one batch of loads; u_kk is its first entry
+            int j0 = 0;
+            double u0 = 0.0;
+            if (lane < ul) {
+                j0 = ldcg_i(P.ucol + (long)k * up + lane);
+                u0 = ldcg_d(P.uval + (long)k * up + lane);
+            }
+            const double wk = __ddiv_rn(val[pos], __shfl_sync(kAll, u0, 0));
             __syncwarp();
             if (fabs(wk) < tau) {  // dropped multiplier
                 if (lane == 0) val[pos] = 0.0;
@@ -163,13 +235,13 @@ __global__ void __launch_bounds__(256) k_ilut(IlutParams P) {
             }
             if (lane == 0) val[pos] = wk;
             __syncwarp();
-            // w_j -= w_k * u_kj for the entries j > k of U row k, 32 at a time
-            for (int qb = 1; qb < ul; qb += 32) {
+            // w_j -= w_k * u_kj for the entries j > k of U row k (q >= 1), 32 at a time
+            for (int qb = 0; qb < ul; qb += 32) {
                 const int q = qb + lane;
-                const bool has = q < ul;
-                int j = 0;
-                double u = 0.0;
-                if (has) {
+                const bool has = q >= 1 && q < ul;
+                int j = j0;
+                double u = u0;
+                if (qb > 0 && has) {
                     j = ldcg_i(P.ucol + (long)k * up + q);
                     u = ldcg_d(P.uval + (long)k * up + q);
                 }
@@ -207,48 +279,23 @@ __global__ void __launch_bounds__(256) k_ilut(IlutParams P) {
             ilut_fail(P, i, lane, failed);
             continue;
         }
-        // drop below tau, keep the p largest of each strict part (ties to the smaller column);
-        // positions follow column order, so the kept entries are written in column order
+        // drop below tau, keep the p largest of each strict part (ties to the smaller column); the
+        // upper part first, so the rows waiting for U row i are released before the lower part
         const int dp = lower_bound(col, 0, len, i);
         const double wd = val[dp];
         if (wd == 0.0) { ilut_fail(P, i, lane, HEC_ERR_ZERO_PIVOT); continue; }
-        int nl = 0, nu = 0;
-        for (int eb = 0; eb < len; eb += 32) {
-            const int e = eb + lane;
-            bool keep = false;
-            const bool lower = e < dp;
-            if (e < len && e != dp) {
-                const double ve = val[e], ae = fabs(ve);
-                if (ve != 0.0 && !(ae < tau)) {
-                    const int b0 = lower ? 0 : dp + 1, b1 = lower ? dp : len;
-                    int rank = 0;
-                    for (int b = b0; b < b1 && rank < P.p; ++b) {
-                        const double vb = val[b], ab = fabs(vb);
-                        if (b == e || vb == 0.0 || ab < tau) continue;
-                        if (ab > ae || (ab == ae && b < e)) ++rank;
-                    }
-                    keep = rank < P.p;
-                }
-            }
-            const unsigned lt = (1u << lane) - 1u;
-            const unsigned kl = __ballot_sync(kAll, keep && lower), ku = __ballot_sync(kAll, keep && !lower);
-            if (keep && lower) {
-                const long o = (long)i * P.p + nl + __popc(kl & lt);
-                P.lcol[o] = col[e];
-                P.lval[o] = val[e];
-            } else if (keep) {
-                const long o = (long)i * up + 1 + nu + __popc(ku & lt);
-                P.ucol[o] = col[e];
-                P.uval[o] = val[e];
-            }
-            nl += __popc(kl);
-            nu += __popc(ku);
-        }
+        int* scol = wc + (cur ^ 1) * cap;
+        double* sval = wv + (cur ^ 1) * cap;
+        const int nu = ilut_select(col, val, dp + 1, len, tau, P.p, lane, scol, sval, P.ucol + (long)i * up + 1,
+                                   P.uval + (long)i * up + 1);
         if (lane == 0) {
             P.ucol[(long)i * up] = i;
             P.uval[(long)i * up] = wd;
         }
-        ilut_publish(P, i, lane, nl, nu + 1);
+        ilut_publish(P, i, lane, nu + 1);
+        const int nl = ilut_select(col, val, 0, dp, tau, P.p, lane, scol, sval, P.lcol + (long)i * P.p,
+                                   P.lval + (long)i * P.p);
+        if (lane == 0) P.llen[i] = nl;
     }
 }
 
