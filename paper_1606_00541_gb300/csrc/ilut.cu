@@ -28,8 +28,8 @@ namespace {
 constexpr unsigned kAll = 0xffffffffu;
 // working-list capacity per warp and warps per block, tried in this order when a row's fill
 // outgrows the list (24 bytes per entry and warp: two column and two value buffers)
-constexpr int kCaps[3] = {240, 1984, 9000};
-constexpr int kWarpsFor[3] = {8, 4, 1};
+constexpr int kCaps[4] = {120, 240, 1984, 9000};
+constexpr int kWarpsFor[4] = {8, 8, 4, 1};
 
 struct IlutParams {
     int n, p;
@@ -375,7 +375,7 @@ HEC_API hec_status ilut_factor(int n, const int* rowptr, const int* col, const d
         const void* k = (const void*)k_ilut;
         int h = 0, cap = 0;
         // a larger working list (fewer warps per block) only when a row's fill outgrew the last one
-        for (int t = 0; t < 3; ++t) {
+        for (int t = 0; t < 4; ++t) {
             cap = kCaps[t];
             const int warps = kWarpsFor[t];
             const size_t smem = (size_t)warps * (24 * (size_t)cap + 128);
