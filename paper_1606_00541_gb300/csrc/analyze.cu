@@ -49,20 +49,54 @@ __global__ void k_levels(int n, const int* __restrict__ rp, const int* __restric
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int chunks = (n + 31) >> 5;
     int mymax = 0;
+    // A chunk is 32 consecutive rows of the lower problem.  A dependency inside the chunk is on an
+    // earlier lane and is resolved with shuffles (one pass over the lanes in order: a lane's level
+    // is final once every lower lane has been broadcast); only dependencies on earlier chunks are
+    // read from memory, polled up to 8 at a time.
     for (int c = gw; c < chunks; c += nw) {
-        int t = (c << 5) + lane;
+        const int base = c << 5;
+        const int t = base + lane;
+        int lev = 0;
+        unsigned intra = 0;  // lanes of this chunk that this row depends on
+        int i = 0;
         if (t < n) {
-            int i = uplo ? n - 1 - t : t;
-            int lev = 0;
-            int a = rp[i], b = rp[i + 1];
+            i = uplo ? n - 1 - t : t;
+            const int a = rp[i], b = rp[i + 1];
+            const int* wl[8];
+            int nwait = 0;
             for (int p = a; p < b; ++p) {
-                int j = __ldg(col + p);
-                bool dep = uplo ? (j > i) : (j < i);
-                if (dep && j >= 0 && j < n) {
-                    int lj = wait_i32(level + j, status, budget);
-                    lev = max(lev, lj + 1);
+                const int j = __ldg(col + p);
+                const bool dep = uplo ? (j > i) : (j < i);
+                if (!dep || j < 0 || j >= n) continue;
+                const int tj = uplo ? n - 1 - j : j;  // its position in the lower problem, < t
+                if (tj >= base) {
+                    intra |= 1u << (tj - base);
+                    continue;
+                }
+                wl[nwait++] = level + j;
+                if (nwait == 8 || p + 1 == b) {
+                    int lv[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) lv[q] = q < nwait ? (int)ld_relaxed_u32(wl[q]) : 0;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (q < nwait) {
+                            const int lj = lv[q] == kSentI ? wait_i32(wl[q], status, budget) : lv[q];
+                            lev = max(lev, lj + 1);
+                        }
+                    nwait = 0;
                 }
             }
+            if (nwait) {
+                for (int q = 0; q < nwait; ++q) lev = max(lev, wait_i32(wl[q], status, budget) + 1);
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 32; ++d) {
+            const int ld = __shfl_sync(0xffffffffu, lev, d);
+            if ((intra >> d) & 1u) lev = max(lev, ld + 1);
+        }
+        if (t < n) {
             publish_i32(level + i, lev);
             mymax = max(mymax, lev + 1);
         }

@@ -50,9 +50,20 @@ __global__ void k_row_counts(int n, const int* __restrict__ rp, const int* __res
     if ((threadIdx.x & 31) == 0) atomicMax(maxcnt, c);
 }
 
-__global__ void k_count_hist(int n, const int* __restrict__ cnt, int* hist) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < n) atomicAdd(hist + cnt[r], 1);
+// histogram of the row counts: few distinct values, so each block counts the small ones in shared
+// memory and adds its totals once (a global atomic per row would serialise on a handful of bins)
+__global__ void k_count_hist(int n, const int* __restrict__ cnt, int nbins, int* hist) {
+    __shared__ int sh[64];
+    for (int t = threadIdx.x; t < 64; t += blockDim.x) sh[t] = 0;
+    __syncthreads();
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const int c = cnt[r];
+        if (c < 64) atomicAdd(sh + c, 1);
+        else atomicAdd(hist + c, 1);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 64 && t < nbins; t += blockDim.x)
+        if (sh[t]) atomicAdd(hist + t, sh[t]);
 }
 
 __global__ void k_tail_len(int n, const int* __restrict__ cnt, int w, int tri, int* tlen) {
@@ -243,7 +254,7 @@ HEC_API hec_status hec_from_csr(int n, const int* rowptr, const int* col, const 
         if ((st = dalloc(&hist, (size_t)maxcnt + 1))) return fail(st);
         cudaMemsetAsync(hist, 0, sizeof(int) * ((size_t)maxcnt + 1), s);
         if (n > 0) {
-            k_count_hist<<<g, 256, 0, s>>>(n, cnt, hist);
+            k_count_hist<<<std::min(g, 4 * num_sms()), 256, 0, s>>>(n, cnt, maxcnt + 1, hist);
             count_launch();
         }
         std::vector<int> h((size_t)maxcnt + 1);

@@ -1105,9 +1105,20 @@ __global__ void k_part_keys(int n, const int* __restrict__ iperm, const int* __r
     key[g] = min(max(pk, 0), nparts - 1);
     val[g] = g;
 }
-__global__ void k_hist(int n, const int* __restrict__ key, int* cnt) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < n) atomicAdd(cnt + key[r], 1);
+// rows per part: a block counts parts below 1024 in shared memory and adds its totals once (one
+// global atomic per row would serialise on the few parts a stretch of sorted keys covers)
+__global__ void k_hist(int n, const int* __restrict__ key, int nparts, int* cnt) {
+    __shared__ int sh[1024];
+    for (int t = threadIdx.x; t < 1024; t += blockDim.x) sh[t] = 0;
+    __syncthreads();
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const int k = key[r];
+        if (k < 1024) atomicAdd(sh + k, 1);
+        else atomicAdd(cnt + k, 1);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 1024 && t < nparts; t += blockDim.x)
+        if (sh[t]) atomicAdd(cnt + t, sh[t]);
 }
 // segment starts: a new segment where the part or the level changes
 __global__ void k_seg_flags(int n, const int* __restrict__ key, const int* __restrict__ rowg,
@@ -1220,7 +1231,7 @@ hec_status build_partition(sptrsv_plan* p, const int* part, int nparts, cudaStre
     if (hbad) return done(set_error(HEC_ERR_INVALID_ARG, "sptrsv_plan_partition: part[] outside [0, nparts)"));
     if ((st = sort_pairs_i32(key, P->rowg, n, nparts - 1, s))) return done(st);
     HEC_CUDA(cudaMemsetAsync(P->part_row, 0, sizeof(int) * ((size_t)nparts + 1), s));
-    k_hist<<<g, 256, 0, s>>>(n, key, P->part_row);
+    k_hist<<<std::min(g, 4 * num_sms()), 256, 0, s>>>(n, key, nparts, P->part_row);
     k_seg_flags<<<g, 256, 0, s>>>(n, key, P->rowg, lv->iperm, lv->level, flag, sigma);
     count_launch(2);
     if ((st = exclusive_scan_i32(P->part_row, P->part_row, nparts, true, s))) return done(st);
