@@ -97,3 +97,22 @@ def test_ilut_preconditioned_fgmres(hec):
     x, info = s.solve(dev(b), rtol=1e-8)
     r = b - oracle.spmv(A, x.cpu().numpy())
     assert info["converged"] and np.linalg.norm(r) <= 1e-8 * np.linalg.norm(b) * 1.0001
+
+
+def test_ilut_structural_diagonal_unsorted_and_empty(hec):
+    # row 1 stores no diagonal: the structural zero slot receives fill (0 - 0.5 * 1) and the
+    # factors equal the oracle's
+    A = (np.array([0, 2, 3], np.int32), np.array([0, 1, 0], np.int32), np.array([2.0, 1.0, 1.0]))
+    Lo, Uo = oracle.ilut(A, 2, 0.0)
+    Lh, Uh = hec.ilut_factor(*[dev(a) for a in A], p=2, tol=0.0)
+    for got, ref in ((host(Lh), Lo), (host(Uh), Uo)):
+        assert all(np.array_equal(g, r) for g, r in zip(got, ref))
+    assert host(Uh)[2][-1] == -0.5
+    # a row with descending columns is rejected
+    B = (np.array([0, 2, 4], np.int32), np.array([1, 0, 0, 1], np.int32), np.array([1.0, 2.0, 1.0, 2.0]))
+    with pytest.raises(hec.HecError):
+        hec.ilut_factor(*[dev(a) for a in B], p=2, tol=0.0)
+    # the empty matrix
+    E = (np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    Lh, Uh = hec.ilut_factor(*[dev(a) for a in E], p=4, tol=1e-3)
+    assert all(len(t) == 0 for t in host(Lh)[1:]) and list(host(Uh)[0]) == [0]
