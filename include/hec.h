@@ -342,13 +342,6 @@ hec_status hec_csr_get(const hec_csr* M, int* n, long long* nnz, const int** row
                        const int** col, const double** val);
 hec_status hec_csr_destroy(hec_csr* M);
 
-/* ILU(k) for k = 0 (pattern of A) or k = 1 (pattern of A plus the fill of level 1: entries
- * (i, j) reached by i -> q -> j with q < min(i, j) both original entries).  Each row i is
- * eliminated IKJ-style: for the pattern columns q < i in ascending order,
- * a_iq <- a_iq / u_qq, then a_ij <- a_ij - a_iq u_qj for pattern columns j > q of both rows.
- * Rows run in the level order of the lower pattern with point-to-point completion waits.
- * Outputs L (unit lower, the 1.0 diagonal stored) and U (upper with its diagonal).  A must have
- * a nonzero diagonal in every row; ZERO_PIVOT if an eliminated pivot is zero.  Synchronizes. */
 /* The lower (uplo 0: j <= i) or upper (uplo 1: j >= i) triangle of a CSR matrix (n x n,
  * ascending columns), without the diagonal when strict != 0, as a device CSR owned by the
  * library.  With it the sweeps run Gauss-Seidel: one forward sweep is (D + L) x' = b - U_s x,
@@ -356,6 +349,13 @@ hec_status hec_csr_destroy(hec_csr* M);
  * the triangular solver, Sec. 1).  Synchronizes `stream`. */
 hec_status csr_triangle(int n, const int* rowptr, const int* col, const double* val, int uplo,
                         int strict, hec_csr** out, void* stream);
+/* ILU(k) for k = 0 (pattern of A) or k = 1 (pattern of A plus the fill of level 1: entries
+ * (i, j) reached by i -> q -> j with q < min(i, j) both original entries).  Each row i is
+ * eliminated IKJ-style: for the pattern columns q < i in ascending order,
+ * a_iq <- a_iq / u_qq, then a_ij <- a_ij - a_iq u_qj for pattern columns j > q of both rows.
+ * Rows run in the level order of the lower pattern with point-to-point completion waits.
+ * Outputs L (unit lower, the 1.0 diagonal stored) and U (upper with its diagonal).  A must have
+ * a nonzero diagonal in every row; ZERO_PIVOT if an eliminated pivot is zero.  Synchronizes. */
 hec_status ilu_factor(int n, const int* rowptr, const int* col, const double* val, int k,
                       hec_csr** L, hec_csr** U, void* stream);
 
