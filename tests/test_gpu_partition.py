@@ -139,3 +139,32 @@ def test_partitioned_timeout_reports_status(hec):
     b = dev(synth.uniform_vector(4096, 1))
     hec.sptrsv_lower(p, b)
     assert hec.STATUS_NAMES[hec.hec_sync_status(p)] == "TIMEOUT"
+
+
+@pytest.mark.parametrize("ras", [False, True])
+def test_partitioned_apply_matches_unpartitioned(hec, ras):
+    """ILU / RAS apply with both plans partitioned (contiguous parts of the extended numbering for
+    RAS, grid boxes for ILU): the same result as the unpartitioned apply, also after the plans are
+    partitioned again."""
+    m = 12
+    A = synth.fv7_lognormal(m, seed=6)
+    Ad = [dev(a) for a in A]
+    n = m ** 3
+    if ras:
+        part, ns = synth.box_partition(m, [5, 7])
+        s = hec.RasSolver(Ad, dev(part), ns, vdt="f64")
+    else:
+        L, U = oracle.ilu0(A)
+        s = hec.IluSolver([dev(a) for a in L], [dev(a) for a in U], A=Ad, vdt="f64")
+    r = dev(synth.uniform_vector(n, 41))
+    ref = s.apply(r).cpu().numpy()
+    nn = s.lvL.n
+    for nb in [(1, 3, 3), (2, 2, 2)]:
+        if ras:
+            s.partition(None, 7)  # contiguous parts of the extended numbering
+        else:
+            bx, _ = synth.grid_boxes(m, nb)
+            s.partition(dev(bx), nb[0] * nb[1] * nb[2])
+        got = s.apply(r).cpu().numpy()
+        assert relmax(got, ref) <= 1e-12
+        assert s.lvL.n == nn
