@@ -33,52 +33,94 @@ __global__ void k_find_diag(int n, const int* __restrict__ rp, const int* __rest
 }
 
 // lu holds A's values on the pattern; on return the factors in place.  done[] zeroed.
-__global__ void k_ilu_numeric(int n, const int* __restrict__ rp, const int* __restrict__ col,
-                              const int* __restrict__ dg, const int* __restrict__ order, double* lu, int* done,
-                              int* status, long long budget) {
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    const int chunks = (n + 31) >> 5;
-    for (int c = gw; c < chunks; c += nw) {
-        const int t = (c << 5) + lane;
-        if (t >= n) continue;
-        const int i = order[t];
-        const int di = dg[i], ei = rp[i + 1];
-        for (int p = rp[i]; p < di; ++p) {
-            const int k = col[p];
-            // wait for row k (bounded)
-            if (ld_acquire_i32(done + k) == 0) {
-                long long t0 = clock64();
-                unsigned it = 0;
-                while (ld_acquire_i32(done + k) == 0) {
-                    if ((++it & 63u) == 0u && (clock64() - t0 > budget || ld_relaxed_u32(status) != 0u)) {
-                        record(status, HEC_ERR_TIMEOUT);
+// One warp per row, rows taken in the level order of the lower pattern (order[t]); the row's
+// columns and values sit in shared memory (rows longer than kIluCap are worked in place in
+// global memory).  For each pivot k < i in ascending order: every lane acquires row k's
+// completion flag, l_ik = a_ik / u_kk, and the lanes split row k's upper entries, each finding
+// its column in row i by binary search and applying a_ij <- fma(-l_ik, u_kj, a_ij).  Every entry
+// receives the same operations in the same order as in a serial IKJ elimination.
+constexpr int kIluCap = 256;
+constexpr int kIluWarps = 8;
+
+__device__ __forceinline__ int lower_bound_i(const int* c, int lo, int hi, int v) {
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (c[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kIluWarps * 32) k_ilu_numeric(int n, const int* __restrict__ rp,
+                                                                const int* __restrict__ col, const int* __restrict__ dg,
+                                                                const int* __restrict__ order, double* lu, int* done,
+                                                                int* status, long long budget) {
+    __shared__ int s_col[kIluWarps][kIluCap];
+    __shared__ double s_val[kIluWarps][kIluCap];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int W = gridDim.x * kIluWarps;
+    for (int t = blockIdx.x * kIluWarps + wl; t < n; t += W) {
+        const int i = __ldg(order + t);
+        const int a = __ldg(rp + i), di = __ldg(dg + i), e = __ldg(rp + i + 1);
+        const int len = e - a, dpos = di - a;
+        const bool sm = len <= kIluCap;
+        const int* rc = sm ? s_col[wl] : col + a;
+        double* rv = sm ? s_val[wl] : lu + a;
+        if (sm) {
+            for (int q = lane; q < len; q += 32) {
+                s_col[wl][q] = __ldg(col + a + q);
+                s_val[wl][q] = lu[a + q];
+            }
+        }
+        __syncwarp();
+        bool bad = false;
+        for (int p = 0; p < dpos; ++p) {
+            const int k = rc[p];
+            // every lane acquires row k (bounded), so its reads of row k are ordered after the release
+            bool ready = ld_acquire_i32(done + k) != 0;
+            if (!__all_sync(full, ready)) {
+                const long long t0 = clock64();
+                for (unsigned it = 1; !__all_sync(full, ready); ++it) {
+                    ready = ld_acquire_i32(done + k) != 0;
+                    if ((it & 63u) == 0u && __any_sync(full, clock64() - t0 > budget || ld_relaxed_u32(status) != 0u)) {
+                        if (lane == 0) record(status, HEC_ERR_TIMEOUT);
+                        bad = true;
                         break;
                     }
                 }
             }
-            const double piv = lu[dg[k]];
+            if (bad) break;
+            const int dk = __ldg(dg + k), ek = __ldg(rp + k + 1);
+            const double piv = lu[dk];
             if (piv == 0.0) {
-                record(status, HEC_ERR_ZERO_PIVOT);
+                if (lane == 0) record(status, HEC_ERR_ZERO_PIVOT);
                 continue;
             }
-            const double lik = lu[p] / piv;
-            lu[p] = lik;
-            int q = dg[k] + 1;
-            const int ek = rp[k + 1];
-            for (int pp = p + 1; pp < ei && q < ek; ++pp) {
-                const int j = col[pp];
-                while (q < ek && col[q] < j) ++q;
-                if (q < ek && col[q] == j) lu[pp] = fma(-lik, lu[q], lu[pp]);
+            const double lik = rv[p] / piv;
+            __syncwarp();
+            if (lane == 0) rv[p] = lik;
+            for (int qb = dk + 1; qb < ek; qb += 32) {
+                const int q = qb + lane;
+                if (q < ek) {
+                    const int j = __ldg(col + q);
+                    const int pos = lower_bound_i(rc, p + 1, len, j);
+                    if (pos < len && rc[pos] == j) rv[pos] = fma(-lik, lu[q], rv[pos]);
+                }
             }
+            __syncwarp();
         }
-        if (lu[di] == 0.0) record(status, HEC_ERR_ZERO_PIVOT);
-        st_release_i32(done + i, 1);
+        if (sm)
+            for (int q = lane; q < len; q += 32) lu[a + q] = s_val[wl][q];
+        __syncwarp();
+        if (lane == 0) {
+            if (rv[dpos] == 0.0) record(status, HEC_ERR_ZERO_PIVOT);
+            __threadfence();
+            st_release_i32(done + i, 1);
+        }
+        __syncwarp();
     }
 }
 
-// L / U row lengths
 __global__ void k_split_len(int n, const int* __restrict__ rp, const int* __restrict__ dg, int* llen, int* ulen) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -346,11 +388,10 @@ HEC_API hec_status ilu_factor(int n, const int* rowptr, const int* col, const do
     if ((st = dalloc(&done, (size_t)n))) return fail(st);
     HEC_CUDA(cudaMemsetAsync(done, 0, sizeof(int) * (size_t)n, s));
     {
-        const int threads = 256;
+        const int threads = kIluWarps * 32;
         int per_sm = max_coop_blocks((const void*)k_ilu_numeric, threads, 0);
         if (per_sm <= 0) return fail(set_error(HEC_ERR_CUDA, "factor kernel cannot be resident"));
-        int chunks = (n + 31) / 32;
-        int blocks = std::max(1, std::min(per_sm * num_sms(), (chunks + 7) / 8));
+        int blocks = std::max(1, std::min(per_sm * num_sms(), (n + kIluWarps - 1) / kIluWarps));
         long long budget = 4000000000LL;
         int nn = n;
         int* status = code + 1;
