@@ -88,6 +88,9 @@ __device__ __forceinline__ void warp_wait(const XT* const (&addr)[NS], typename 
     typedef Word<XT> W;
     if (!__any_sync(kFull, pending)) return;
     const long long t0 = clock64();
+    // the status word as read at the previous check: its load is issued there and only used
+    // here, so a check does not stall the poll loop for an L2 round trip
+    unsigned failed = 0u;
     for (unsigned it = 1;; ++it) {
         if (backoff_ns) __nanosleep(backoff_ns);
 #pragma unroll
@@ -99,7 +102,7 @@ __device__ __forceinline__ void warp_wait(const XT* const (&addr)[NS], typename 
         }
         if (!__any_sync(kFull, pending)) return;
         if ((it & 31u) == 0u) {
-            bool give_up = (clock64() - t0 > budget) || (ld_relaxed_u32(status) != 0u);
+            const bool give_up = (clock64() - t0 > budget) || failed != 0u;
             if (__any_sync(kFull, give_up)) {
                 record(status, HEC_ERR_TIMEOUT);
 #pragma unroll
@@ -107,6 +110,7 @@ __device__ __forceinline__ void warp_wait(const XT* const (&addr)[NS], typename 
                     if (pending & (1u << k)) raw[k] = 0;
                 return;
             }
+            failed = ld_relaxed_u32(status);
         }
     }
 }
@@ -427,12 +431,14 @@ struct DepBatchV {
     __device__ __forceinline__ void wait(int* status, long long budget, int backoff_ns) {
         if (!__any_sync(kFull, pend)) return;
         const long long t0 = clock64();
+        unsigned failed = 0u;  // the status word as read at the previous check
         for (unsigned it = 1;; ++it) {
             if (backoff_ns) __nanosleep(backoff_ns);
             poll();
             if (!__any_sync(kFull, pend)) return;
             if ((it & 31u) == 0u) {
-                bool give_up = (clock64() - t0 > budget) || (ld_relaxed_u32(status) != 0u);
+                const bool give_up = (clock64() - t0 > budget) || failed != 0u;
+                failed = ld_relaxed_u32(status);
                 if (__any_sync(kFull, give_up)) {
                     record(status, HEC_ERR_TIMEOUT);
 #pragma unroll
@@ -580,6 +586,7 @@ struct PartParams {
     const int* __restrict__ part_row;
     const int* __restrict__ part_chunk;
     const int2* __restrict__ chunks;
+    const void* __restrict__ bp;  // b gathered into plan order in the work type (k_part_prep)
     const double* __restrict__ b;
     int ldb;
     const int* __restrict__ gather;
@@ -592,12 +599,26 @@ struct PartParams {
     int skip_row;
 };
 
-// dependencies of one lane, each either in this part's shared memory or in the global solution
+// Volatile shared-memory word loads by shared-window address, so a local poll is always a
+// shared-memory load whatever the compiler can infer about the pointer.
+__device__ __forceinline__ unsigned int ld_shared_u32(unsigned int a) {
+    unsigned int v;
+    asm volatile("ld.volatile.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_shared_u64(unsigned int a) {
+    unsigned long long v;
+    asm volatile("ld.volatile.shared.b64 %0, [%1];" : "=l"(v) : "r"(a));
+    return v;
+}
+
+// dependencies of one lane, each either in this part's shared memory (shared-window byte
+// address) or in the global solution (row index)
 template <typename XT, typename AT, int NS>
 struct DepBatchP {
     typedef Word<XT> W;
     typedef typename W::T WT;
-    const WT* addr[NS];
+    unsigned int where[NS];
     WT raw[NS];
     AT v[NS];
     unsigned valid, pend, local;
@@ -605,39 +626,67 @@ struct DepBatchP {
         valid = pend = local = 0;
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
-            addr[k] = nullptr;
+            where[k] = 0;
             raw[k] = 0;
             v[k] = AT(0);
         }
     }
-    __device__ __forceinline__ void set(int k, const XT* xp, const WT* sxp, int cc, int lo, int hi, AT coef) {
+    // sbase: shared-window address of the part's solution, whose rows are lo .. hi-1
+    __device__ __forceinline__ void set(int k, unsigned int sbase, int cc, int lo, int hi, AT coef) {
         v[k] = coef;
         valid |= 1u << k;
         pend |= 1u << k;
         if (cc >= lo && cc < hi) {
-            addr[k] = sxp + (cc - lo);
+            where[k] = sbase + (unsigned int)(cc - lo) * (unsigned int)sizeof(WT);
             local |= 1u << k;
         } else {
-            addr[k] = (const WT*)(xp + cc);
+            where[k] = (unsigned int)cc;
         }
     }
-    __device__ __forceinline__ void poll() {
+    __device__ __forceinline__ void poll(const XT* xp) {
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
             if (pend & (1u << k)) {
-                raw[k] = (local & (1u << k)) ? *(const volatile WT*)addr[k] : W::load((const XT*)addr[k]);
+                if (local & (1u << k))
+                    raw[k] = sizeof(WT) == 8 ? (WT)ld_shared_u64(where[k]) : (WT)ld_shared_u32(where[k]);
+                else
+                    raw[k] = W::load(xp + where[k]);
                 if (raw[k] != W::kSent) pend &= ~(1u << k);
             }
         }
     }
-    __device__ __forceinline__ void wait(int* status, long long budget) {
+    __device__ __forceinline__ void wait(const XT* xp, int* status, long long budget) {
         if (!__any_sync(kFull, pend)) return;
         const long long t0 = clock64();
+        unsigned failed = 0u;  // the status word as read at the previous check
+        // First spin on one word a lane: its latest outstanding local dependency (the largest
+        // row index, so the highest level; rows are in level order).  One shared load per
+        // iteration instead of one per slot keeps the polls of the waiting warps from crowding
+        // the shared-memory pipe that the producers' stores and the other polls go through.
+        // A warp with an outstanding dependency in another part keeps polling every slot, so
+        // the L2 round trip of that poll overlaps the local waits.
+        unsigned int last = 0u;
+        const unsigned lp = pend & local;
+#pragma unroll
+        for (int k = 0; k < NS; ++k)
+            if ((lp & (1u << k)) && where[k] > last) last = where[k];
+        if (__any_sync(kFull, lp != 0u) && !__any_sync(kFull, (pend & ~local) != 0u)) {
+            for (unsigned it = 1;; ++it) {
+                const bool ok = lp == 0u || (sizeof(WT) == 8 ? (WT)ld_shared_u64(last) : (WT)ld_shared_u32(last)) != W::kSent;
+                if (__all_sync(kFull, ok)) break;
+                if ((it & 63u) == 0u) {
+                    const bool give_up = (clock64() - t0 > budget) || failed != 0u;
+                    failed = ld_relaxed_u32(status);
+                    if (__any_sync(kFull, give_up)) break;  // the loop below records the failure
+                }
+            }
+        }
         for (unsigned it = 1;; ++it) {
-            poll();
+            poll(xp);
             if (!__any_sync(kFull, pend)) return;
             if ((it & 63u) == 0u) {
-                bool give_up = (clock64() - t0 > budget) || (ld_relaxed_u32(status) != 0u);
+                const bool give_up = (clock64() - t0 > budget) || failed != 0u;
+                failed = ld_relaxed_u32(status);
                 if (__any_sync(kFull, give_up)) {
                     record(status, HEC_ERR_TIMEOUT);
 #pragma unroll
@@ -656,13 +705,79 @@ struct DepBatchP {
     }
 };
 
+// One lane's row of a chunk of the partitioned sweep: everything but the dependencies, loaded
+// for the warp's next chunk while it waits on the current one.  The loads are all one step from
+// the row index (the right-hand side is gathered into plan order before the sweep) and nothing
+// here uses a loaded value: widening, the tail length and the scatter index are derived when the
+// chunk is processed, so issuing the prefetch never stalls the warp.  Slab values are loaded
+// whether or not the slot is padding (padding is in bounds and zero).
+template <typename VT, typename AT> __device__ __forceinline__ AT widen_v(VT v) { return (AT)v; }
+template <> __device__ __forceinline__ float widen_v<__nv_bfloat16, float>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename VT, typename XT, typename AT, int NP>
+struct PartRow {
+    AT b;            // right-hand side
+    XT d;            // reciprocal diagonal
+    int g, t0, t1;   // factor row (-1: idle lane), tail range [t0, t1) with the diagonal last
+    int cc[NP > 0 ? NP : 1];
+    VT v[NP > 0 ? NP : 1];
+    __device__ __forceinline__ void load(const PartParams& p, int2 ch, int lane, bool have) {
+        b = AT(0);
+        d = XT(1);
+        g = -1;
+        t0 = 0;
+        t1 = 1;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            cc[k] = -1;
+            v[k] = VT(0.0f);
+        }
+        if (have && lane < ch.y) {
+            const int r = ch.x + lane;
+            g = __ldg(p.rowg + r);
+            b = __ldg((const AT*)p.bp + r);
+            t0 = __ldg(p.tptr + r);
+            t1 = __ldg(p.tptr + r + 1);
+            d = __ldg((const XT*)p.dinv + r);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                if (k < p.w) {
+                    const long s = (long)k * p.ld + r;
+                    cc[k] = __ldg(p.ell_col + s);
+                    v[k] = __ldg((const VT*)p.ell_val + s);
+                }
+            }
+        }
+    }
+};
+
+// Before a partitioned sweep: the level-ordered solution set to the sentinel, and the right-hand
+// side gathered into plan order in the work type.
+template <typename XT>
+__global__ void k_part_prep(int n, XT* xp, const int* __restrict__ rowg, const int* __restrict__ gather,
+                            const double* __restrict__ b, int ldb, typename Acc<XT>::T* bp) {
+    const int st = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) {
+        if (sizeof(XT) == 8) ((unsigned long long*)xp)[i] = kSent64;
+        else ((unsigned int*)xp)[i] = kSent32;
+        const int g = __ldg(rowg + i);
+        const int gr = gather ? __ldg(gather + g) : g;
+        bp[i] = (typename Acc<XT>::T)__ldg(b + (long)gr * ldb);
+    }
+}
+
 template <typename VT, typename XT, int WMAX>
 __global__ void __launch_bounds__(1024, 1) k_sweep_part(PartParams p) {
     typedef typename Acc<XT>::T AT;
     typedef Word<XT> W;
     typedef typename W::T WT;
+    // slab slots carried in the prefetched row: all four of a narrow FP32 slab, fewer where the
+    // registers of a 1024-thread block (64 a thread) would otherwise spill
+    constexpr int NP = WMAX > 4 ? 0 : sizeof(AT) == 8 ? 2 : WMAX;
+    constexpr bool PF = WMAX <= 4 || sizeof(AT) == 4;  // FP64 with a wide slab loads at the chunk
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WT* sxp = (WT*)smem_raw;
+    const unsigned int sbase = (unsigned int)__cvta_generic_to_shared(smem_raw);
     const int part = blockIdx.x;
     const int lo = __ldg(p.part_row + part), hi = __ldg(p.part_row + part + 1);
     for (int i = threadIdx.x; i < hi - lo; i += blockDim.x) sxp[i] = W::kSent;
@@ -672,38 +787,42 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_part(PartParams p) {
     const VT* __restrict__ ev = (const VT*)p.ell_val;
     const VT* __restrict__ tv = (const VT*)p.tval;
     XT* xp = (XT*)p.xp;
-    // the warp's next chunk entry is fetched while it works on the current one, so the chain of
-    // dependent loads that starts a chunk (entry -> row data -> b) is one link shorter
-    int2 ch_next = c0 + warp < c1 ? __ldg(p.chunks + c0 + warp) : make_int2(0, 0);
+    // chunk entries run two chunks ahead of the warp, row data one chunk ahead
+    int2 ch_a = c0 + warp < c1 ? __ldg(p.chunks + c0 + warp) : make_int2(0, 0);
+    int2 ch_b = c0 + warp + nwarps < c1 ? __ldg(p.chunks + c0 + warp + nwarps) : make_int2(0, 0);
+    PartRow<VT, XT, AT, NP> nxt, row;
+    if (PF) nxt.load(p, ch_a, lane, c0 + warp < c1);
     for (int c = c0 + warp; c < c1; c += nwarps) {
-        const int2 ch = ch_next;
-        if (c + nwarps < c1) ch_next = __ldg(p.chunks + c + nwarps);
+        const int2 ch = ch_a;
+        ch_a = ch_b;
+        if (c + 2 * nwarps < c1) ch_b = __ldg(p.chunks + c + 2 * nwarps);
+        if (PF) {
+            row = nxt;
+            nxt.load(p, ch_a, lane, c + nwarps < c1);
+        } else {
+            row.load(p, ch, lane, true);
+        }
         const int r = ch.x + lane;
         const bool act = lane < ch.y;
-        AT acc = AT(0), diag = AT(1);
-        int t0 = 0, tl = 0, sr = -1;
-        if (act) {
-            const int g = __ldg(p.rowg + r);
-            const int gr = p.gather ? __ldg(p.gather + g) : g;
-            acc = (AT)__ldg(p.b + (long)gr * p.ldb);
-            t0 = __ldg(p.tptr + r);
-            tl = __ldg(p.tptr + r + 1) - 1 - t0;
-            diag = (AT)__ldg((const XT*)p.dinv + r);
-            sr = p.scatter ? __ldg(p.scatter + g) : g;
-        }
+        AT acc = row.b;
+        const AT diag = (AT)row.d;
+        const int t0 = row.t0, tl = row.t1 - 1 - row.t0;
+        const int sr = row.g < 0 ? -1 : p.scatter ? __ldg(p.scatter + row.g) : row.g;
         DepBatchP<XT, AT, WMAX> slab;
         slab.clear();
 #pragma unroll
         for (int k = 0; k < WMAX; ++k) {
-            if (act && k < p.w) {
+            if (k < NP) {
+                if (row.cc[k] >= 0) slab.set(k, sbase, row.cc[k], lo, hi, widen_v<VT, AT>(row.v[k]));
+            } else if (act && k < p.w) {
                 const long s = (long)k * p.ld + r;
                 const int cc = __ldg(p.ell_col + s);
-                if (cc >= 0) slab.set(k, xp, sxp, cc, lo, hi, ldv<VT, AT>(ev + s));
+                if (cc >= 0) slab.set(k, sbase, cc, lo, hi, ldv<VT, AT>(ev + s));
             }
         }
         const int tmax = __reduce_max_sync(kFull, tl);
-        slab.poll();
-        slab.wait(p.status, p.budget);
+        slab.poll(xp);
+        slab.wait(xp, p.status, p.budget);
         acc = slab.accumulate(acc);
         for (int kb = WMAX; kb < p.w; kb += kTailBatch) {  // wider slabs, kTailBatch slots at a time
             DepBatchP<XT, AT, kTailBatch> more;
@@ -714,11 +833,11 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_part(PartParams p) {
                 if (act && k < p.w) {
                     const long s = (long)k * p.ld + r;
                     const int cc = __ldg(p.ell_col + s);
-                    if (cc >= 0) more.set(j, xp, sxp, cc, lo, hi, ldv<VT, AT>(ev + s));
+                    if (cc >= 0) more.set(j, sbase, cc, lo, hi, ldv<VT, AT>(ev + s));
                 }
             }
-            more.poll();
-            more.wait(p.status, p.budget);
+            more.poll(xp);
+            more.wait(xp, p.status, p.budget);
             acc = more.accumulate(acc);
         }
         for (int tb = 0; tb < tmax; tb += kTailBatch) {
@@ -727,21 +846,20 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_part(PartParams p) {
 #pragma unroll
             for (int k = 0; k < kTailBatch; ++k)
                 if (tb + k < tl)
-                    tail.set(k, xp, sxp, __ldg(p.tcol + t0 + tb + k), lo, hi, ldv<VT, AT>(tv + t0 + tb + k));
-            tail.poll();
-            tail.wait(p.status, p.budget);
+                    tail.set(k, sbase, __ldg(p.tcol + t0 + tb + k), lo, hi, ldv<VT, AT>(tv + t0 + tb + k));
+            tail.poll(xp);
+            tail.wait(xp, p.status, p.budget);
             acc = tail.accumulate(acc);
         }
-        if (act) {
-            const AT xr = acc * diag;
+        const AT xr = acc * diag;
+        const bool pub = act && r != p.skip_row;
+        if (pub) {
             WT wv = sizeof(XT) == 8 ? (WT)__double_as_longlong((double)(XT)xr) : (WT)__float_as_uint((float)(XT)xr);
             if (wv == W::kSent) wv = sizeof(XT) == 8 ? (WT)0x7FF8000000000000ull : (WT)0x7FC00000u;
-            if (r != p.skip_row) {
-                *(volatile WT*)(sxp + (r - lo)) = wv;  // consumers in this part
-                publish_x(xp + r, (XT)xr);             // consumers in other parts
-            }
-            if (sr >= 0) p.x[(long)sr * p.ldx] = (double)xr;
+            *(volatile WT*)(sxp + (r - lo)) = wv;  // consumers in this part
         }
+        if (pub) publish_x(xp + r, (XT)xr);  // consumers in other parts
+        if (act && sr >= 0) p.x[(long)sr * p.ldx] = (double)xr;
     }
 }
 
@@ -969,7 +1087,8 @@ hec_status launch_part(const sptrsv_plan* pl, PartParams& pp, cudaStream_t s) {
     const int fb = (int)std::min(4096L, std::max(1L, (count + 255) / 256));
     {
         ProfScope ps_(s, PROF_FILL);
-        k_fill_sentinel<XT><<<fb, 256, 0, s>>>((XT*)pp.xp, count);
+        k_part_prep<XT><<<fb, 256, 0, s>>>((int)count, (XT*)pp.xp, P->rowg, pp.gather, pp.b, pp.ldb,
+                                           (typename Acc<XT>::T*)P->bp);
     }
     HEC_LAUNCHED();
     void* args[] = {&pp};
@@ -1014,6 +1133,7 @@ hec_status sweep(const sptrsv_plan* pl, int nrhs, const double* b, int ldb, cons
         pp.part_row = P->part_row;
         pp.part_chunk = P->part_chunk;
         pp.chunks = P->chunks;
+        pp.bp = P->bp;
         pp.b = b;
         pp.ldb = ldb;
         pp.gather = gather;
@@ -1077,6 +1197,7 @@ void free_part(hec_part_data* P) {
     if (!P) return;
     cudaFree(P->rowg); cudaFree(P->part_row); cudaFree(P->part_seg); cudaFree(P->seg_start);
     cudaFree(P->ell_col); cudaFree(P->ell_val); cudaFree(P->tptr); cudaFree(P->tcol); cudaFree(P->tval); cudaFree(P->dinv);
+    cudaFree(P->bp); cudaFree(P->part_chunk); cudaFree(P->chunks);
     delete P;
 }
 
@@ -1269,7 +1390,7 @@ hec_status build_partition(sptrsv_plan* p, const int* part, int nparts, cudaStre
     const size_t ws = T->vdt == HEC_F64 ? 8 : 4;
     if ((st = dalloc(&P->ell_col, (size_t)T->w * T->ld)) || (st = dmalloc(&P->ell_val, vs * (size_t)T->w * T->ld + 16)) ||
         (st = dalloc(&P->tcol, (size_t)T->tail_nnz)) || (st = dmalloc(&P->tval, vs * (size_t)T->tail_nnz + 16)) ||
-        (st = dmalloc(&P->dinv, ws * (size_t)n + 16)))
+        (st = dmalloc(&P->dinv, ws * (size_t)n + 16)) || (st = dmalloc(&P->bp, ws * (size_t)n + 16)))
         return done(st);
     const int gl = (T->ld + 255) / 256;
     if (T->vdt == HEC_F64) {

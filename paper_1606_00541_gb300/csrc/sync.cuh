@@ -51,14 +51,16 @@ __device__ __forceinline__ void record(int* status, int code) {
 template <typename Word, typename Load>
 __device__ __noinline__ Word spin_until_not(const void* p, Word sentinel, int* status, long long budget, Load load) {
     long long t0 = clock64();
+    unsigned failed = 0u;  // the status word as read at the previous check (not waited on)
     for (unsigned it = 1;; ++it) {
         Word v = load(p);
         if (v != sentinel) return v;
         if ((it & 63u) == 0u) {
-            if (clock64() - t0 > budget || (status && ld_relaxed_u32(status) != 0u)) {
+            if (clock64() - t0 > budget || failed != 0u) {
                 record(status, HEC_ERR_TIMEOUT);
                 return Word(0);
             }
+            if (status) failed = ld_relaxed_u32(status);
         }
     }
 }
