@@ -309,6 +309,11 @@ def main():
                 "peak_source": src,
                 "sweep_share_of_step": (sweep_ms / 1000.0) / elapsed,
                 "avg_sweep_us": avg_launch_s * 1e6, "bytes_per_sweep": per_sweep}
+    if args.sweep == "part":
+        # the second bound: the dependency chain at the schedule's own measured hop latencies
+        lf = level_floor(hec, torch, devn, s.lvL.nlev, sum(k - 1 for k in sweep_grid(m)), PART_THREADS)
+        lf["frac"] = lf["floor_us"] / (avg_launch_s * 1e6)
+        roofline["latency_floor"] = lf
 
     # e2e: host buffers through the public API, copies inside the timed region
     host = [a.cpu().pin_memory() for a in (*Ad, *L, *U, bd)]
@@ -485,14 +490,61 @@ def pick_schedule(hec, torch, s, m, b, reps=5):
     return "global (L+U %.0f us; partitioned %.0f us)" % (tg * 1e6, tp * 1e6)
 
 
+def level_floor(hec, torch, device, levels, crossings, threads, vdt="f32", n=4096, reps=10):
+    """The level-latency bound of the partitioned sweep, measured with its own synchronisation (an
+    empty-level micro-benchmark): a bidiagonal lower factor of n rows (one row and one dependency
+    per level) swept as one part gives the in-part hop t_local; with its rows alternating between
+    two parts every dependency crosses, which gives the cross-part hop t_cross.  A sweep of
+    `levels` levels whose chain crosses `crossings` part boundaries cannot finish in less than
+    (levels - crossings) t_local + crossings t_cross.  Kernel-only times (library event profile)."""
+    import numpy as np
+    col = np.empty(2 * n - 1, np.int32)
+    col[0] = 0
+    col[1::2] = np.arange(0, n - 1)
+    col[2::2] = np.arange(1, n)
+    val = np.empty(2 * n - 1)
+    val[0] = 1.0
+    val[1::2] = -0.5
+    val[2::2] = 1.0
+    rp = np.concatenate([[0], np.arange(1, 2 * n, 2)]).astype(np.int32)
+    rp_d, ci_d, v_d = (torch.as_tensor(a, device=device) for a in (rp, col, val))
+    lv = hec.sptrsv_analyze(rp_d, ci_d, 0)
+    plan = hec.sptrsv_plan_create(hec.hec_from_csr(rp_d, ci_d, v_d, levels=lv, vdt=vdt), lv)
+    b = torch.ones(n, dtype=torch.float64, device=device)
+    x = torch.empty_like(b)
+    hop = {}
+    for name, part, nparts in (("t_local_us", torch.zeros(n, dtype=torch.int32, device=device), 1),
+                               ("t_cross_us", (torch.arange(n, device=device) % 2).to(torch.int32), 2)):
+        hec.sptrsv_plan_partition(plan, part, nparts, threads)
+        for _ in range(3):
+            hec.sptrsv_lower(plan, b, x)
+        torch.cuda.synchronize()
+        hec.profile_enable(True)
+        hec.profile_read(reset=True)
+        for _ in range(reps):
+            hec.sptrsv_lower(plan, b, x)
+        torch.cuda.synchronize()
+        ms, nl = hec.profile_read(reset=True)
+        hec.profile_enable(False)
+        hop[name] = ms * 1000.0 / max(nl, 1) / n
+    floor = (levels - crossings) * hop["t_local_us"] + crossings * hop["t_cross_us"]
+    return {"levels": levels, "crossings": crossings, **hop, "floor_us": floor,
+            "method": "bidiagonal chain of %d rows, one part / two alternating parts, %d threads" % (n, threads)}
+
+
 def sweep_partition(torch, m, device):
     """x-pencils for the partitioned single-RHS sweep: the y-z plane cut into 12 x 12 boxes (144
     parts, one resident 1024-thread block each), so a dependency chain crosses a part boundary at
     most 22 times and every other step stays in one SM's shared memory.  Grids above 160^3 take
     8 x 19 pencils (152 parts) so that a part's FP32 solution still fits in shared memory."""
     from paper_1606_00541_gb300 import synth
-    part, nparts = synth.grid_boxes(m, (1, 12, 12) if m <= 160 else (1, 8, 19))
+    part, nparts = synth.grid_boxes(m, sweep_grid(m))
     return torch.as_tensor(part, device=device), nparts
+
+
+def sweep_grid(m):
+    """Boxes per axis of the x-pencil partition used on an m^3 grid."""
+    return (1, 12, 12) if m <= 160 else (1, 8, 19)
 
 
 def ras_cuts(m):
