@@ -10,7 +10,8 @@ each, same results up to summation order); `--sweep global` times the global lev
 ILU(0) factors are computed once on the GPU before timing.  Inputs are seeded and synthetic
 (ln k ~ N(0, 2^2), b = A x_true with x_true ~ U[-1, 1]); the working set (~1 GB) is larger than L2.
 
-Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle instead.
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle instead, on a bounded
+sample of the same workload scaled to the GPU run's iteration count (the paper ships no code to run).
 """
 from __future__ import annotations
 
