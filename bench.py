@@ -270,7 +270,7 @@ def main():
         dist.barrier()
     clocks = Clocks(local)
     clocks.start()
-    hec.profile_enable(True)
+    hec.profile_enable(True, categories=[0])  # event records around the sweep launches only
     hec.profile_read(reset=True)
     l0 = hec.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

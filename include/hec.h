@@ -67,6 +67,11 @@ long long hec_launch_count(void);
  * recorded events and returns the summed device time (ms) and the number of sweep launches
  * since the last reset (reset != 0 clears the record).  Off by default. */
 hec_status hec_profile_enable(int on);
+/* Enables the record for the categories in `mask` only (bit c = category c of
+ * hec_profile_read_category; 0 disables), so a timed run can bracket just the kernels it reports
+ * and leave the rest of the launch stream without event records.  hec_profile_enable(on) is
+ * mask = all or none. */
+hec_status hec_profile_enable_categories(unsigned int mask);
 hec_status hec_profile_read(double* sweep_ms, long long* sweep_launches, int reset);
 /* The same record for other kernel classes (not reset): 0 sweeps, 1 SpMV, 2 Gram-Schmidt dots
  * and updates, 3 the small Arnoldi kernels, 4 vector scale/copy/update, 5 sentinel fills. */

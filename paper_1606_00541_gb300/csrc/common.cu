@@ -168,16 +168,16 @@ struct ProfEntry {
     int cat;
 };
 std::mutex g_prof_mu;
-bool g_prof_on = false;
+unsigned int g_prof_mask = 0u;  // bit c: category c is recorded
 std::vector<ProfEntry> g_prof_used;
 std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_free;
 }  // namespace
 
-bool profiling() { return g_prof_on; }
+bool profiling() { return g_prof_mask != 0u; }
 
 void profile_begin(cudaStream_t s, void** token, int cat) {
     *token = nullptr;
-    if (!g_prof_on) return;
+    if (!(g_prof_mask & (1u << cat))) return;
     std::lock_guard<std::mutex> g(g_prof_mu);
     std::pair<cudaEvent_t, cudaEvent_t> ev;
     if (!g_prof_free.empty()) {
@@ -218,7 +218,12 @@ static void prof_sum(int cat, double* ms_out, long long* n_out) {
 }  // namespace hec
 
 HEC_API hec_status hec_profile_enable(int on) {
-    hec::g_prof_on = on != 0;
+    hec::g_prof_mask = on != 0 ? 0xFFFFFFFFu : 0u;
+    return HEC_OK;
+}
+
+HEC_API hec_status hec_profile_enable_categories(unsigned int mask) {
+    hec::g_prof_mask = mask;
     return HEC_OK;
 }
 

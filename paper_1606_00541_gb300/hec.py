@@ -118,11 +118,17 @@ def _nrhs(t):
 
 
 _hec_profile_enable = _sig("hec_profile_enable", _i)
+_hec_profile_enable_categories = _sig("hec_profile_enable_categories", ctypes.c_uint)
 _hec_profile_read = _sig("hec_profile_read", ctypes.POINTER(_d), ctypes.POINTER(_ll), _i)
 
 
-def profile_enable(on=True):
-    _check(_hec_profile_enable(1 if on else 0), "hec_profile_enable")
+def profile_enable(on=True, categories=None):
+    """Kernel timing by category (include/hec.h): all categories, or only those listed
+    (0 sweeps, 1 SpMV, 2 Gram-Schmidt, 3 Arnoldi, 4 vector kernels, 5 sentinel fills)."""
+    if categories is None or not on:
+        _check(_hec_profile_enable(1 if on else 0), "hec_profile_enable")
+    else:
+        _check(_hec_profile_enable_categories(sum(1 << int(c) for c in categories)), "hec_profile_enable_categories")
 
 
 _hec_profile_read_category = _sig("hec_profile_read_category", _i, ctypes.POINTER(_d), ctypes.POINTER(_ll))
