@@ -672,8 +672,18 @@ struct DepBatchP {
             if ((lp & (1u << k)) && where[k] > last) last = where[k];
         if (__any_sync(kFull, lp != 0u) && !__any_sync(kFull, (pend & ~local) != 0u)) {
             for (unsigned it = 1;; ++it) {
-                const bool ok = lp == 0u || (sizeof(WT) == 8 ? (WT)ld_shared_u64(last) : (WT)ld_shared_u32(last)) != W::kSent;
-                if (__all_sync(kFull, ok)) break;
+                const WT lv = lp == 0u ? (WT)0 : (sizeof(WT) == 8 ? (WT)ld_shared_u64(last) : (WT)ld_shared_u32(last));
+                if (__all_sync(kFull, lp == 0u || lv != W::kSent)) {
+                    // the spun-on word is published: it is that dependency's value, so only the
+                    // lane's other outstanding words need the poll below
+#pragma unroll
+                    for (int k = 0; k < NS; ++k)
+                        if ((lp & (1u << k)) && where[k] == last) {
+                            raw[k] = lv;
+                            pend &= ~(1u << k);
+                        }
+                    break;
+                }
                 if ((it & 63u) == 0u) {
                     const bool give_up = (clock64() - t0 > budget) || failed != 0u;
                     failed = ld_relaxed_u32(status);
