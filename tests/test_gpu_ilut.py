@@ -34,6 +34,9 @@ CASES = [
     ("random_600", lambda: synth.random_sparse(600, 0.01, 7), 20, 1e-4),
     ("p0_diagonal_only", lambda: synth.fv7_lognormal(6, seed=5), 0, 1e-3),
     ("exact_lu_poisson2d_8", lambda: synth.poisson2d_5pt(8), 64, 0.0),
+    ("hand_worked_4x4", lambda: (np.array([0, 3, 6, 9, 12], np.int32),
+                                 np.array([0, 1, 2, 0, 1, 3, 0, 1, 2, 1, 2, 3], np.int32),
+                                 np.array([4.0, 1.0, 1.0, 2.0, 5.0, 1.0, 0.3, 3.0, 6.0, 1.0, 0.01, 8.0])), 1, 0.01),
 ]
 
 

@@ -437,6 +437,34 @@ def test_ilut_limits(orc):
             assert all(abs(v) >= tau[i] for _, v in off)
 
 
+def test_ilut_hand_worked_example(orc):
+    """ILUT(p = 1, tol = 0.01) (Sec. 3; Saad's dual threshold) on a 4 x 4 matrix, factors worked
+    by hand.  tau_i = tol * ||a_i||_2 of the original row; a multiplier below tau is dropped
+    before it updates the row; after the row's elimination the p largest of each part survive
+    (ties to the smaller column).  Row 0: the tie between columns 1 and 2 keeps column 1.  Row 2:
+    the multiplier 0.3 / 4 = 0.075 passes tau_2 = 0.0671 (with a 1-norm tau, 0.093, it would be
+    dropped), updates column 1 to 3 - 0.075 = 2.925, and is then dropped by p; (2,1) = 2.925 / 4.5
+    = 0.65 and the fill (2,3) = -0.65.  Row 3: the multiplier 0.01 / 6 is below tau_3 = 0.0806 and
+    is dropped before updating, so u33 = 8 - 1 / 4.5."""
+    A = csr_of(np.array([[4.0, 1.0, 1.0, 0.0],
+                         [2.0, 5.0, 0.0, 1.0],
+                         [0.3, 3.0, 6.0, 0.0],
+                         [0.0, 1.0, 0.01, 8.0]]))
+    L, U = orc.ilut(A, 1, 0.01)
+    L_hand = np.array([[1.0, 0.0, 0.0, 0.0],
+                       [0.5, 1.0, 0.0, 0.0],
+                       [0.0, 0.65, 1.0, 0.0],
+                       [0.0, 0.2222222222222222, 0.0, 1.0]])
+    U_hand = np.array([[4.0, 1.0, 0.0, 0.0],
+                       [0.0, 4.5, 0.0, 1.0],
+                       [0.0, 0.0, 6.0, -0.65],
+                       [0.0, 0.0, 0.0, 7.777777777777778]])
+    assert np.abs(dense(L) - L_hand).max() <= 1e-15
+    assert np.abs(dense(U) - U_hand).max() <= 1e-15
+    # the kept pattern exactly (no explicit zeros where the hand factors are zero)
+    assert list(L[1]) == [0, 0, 1, 1, 2, 1, 3] and list(U[1]) == [0, 1, 1, 3, 2, 3, 3]
+
+
 def test_ilut_tridiagonal_equals_ilu0(orc):
     n = 20
     D = np.diag(np.full(n, 3.0)) + np.diag(np.full(n - 1, -1.0), 1) + np.diag(np.full(n - 1, -1.2), -1)
