@@ -491,13 +491,10 @@ def pick_schedule(hec, torch, s, m, b, reps=5):
     return "global (L+U %.0f us; partitioned %.0f us)" % (tg * 1e6, tp * 1e6)
 
 
-def level_floor(hec, torch, device, levels, crossings, threads, vdt="f32", n=4096, reps=10):
-    """The level-latency bound of the partitioned sweep, measured with its own synchronisation (an
-    empty-level micro-benchmark): a bidiagonal lower factor of n rows (one row and one dependency
-    per level) swept as one part gives the in-part hop t_local; with its rows alternating between
-    two parts every dependency crosses, which gives the cross-part hop t_cross.  A sweep of
-    `levels` levels whose chain crosses `crossings` part boundaries cannot finish in less than
-    (levels - crossings) t_local + crossings t_cross.  Kernel-only times (library event profile)."""
+def chain_csr(n):
+    """CSR of the lower bidiagonal chain used by level_floor: row 0 holds only
+    its diagonal, row i > 0 holds (i-1, i); so row i is at level i and every level has one row
+    with one dependency."""
     import numpy as np
     col = np.empty(2 * n - 1, np.int32)
     col[0] = 0
@@ -508,7 +505,17 @@ def level_floor(hec, torch, device, levels, crossings, threads, vdt="f32", n=409
     val[1::2] = -0.5
     val[2::2] = 1.0
     rp = np.concatenate([[0], np.arange(1, 2 * n, 2)]).astype(np.int32)
-    rp_d, ci_d, v_d = (torch.as_tensor(a, device=device) for a in (rp, col, val))
+    return rp, col, val
+
+
+def level_floor(hec, torch, device, levels, crossings, threads, vdt="f32", n=4096, reps=10):
+    """The level-latency bound of the partitioned sweep, measured with its own synchronisation (an
+    empty-level micro-benchmark): a bidiagonal lower factor of n rows (one row and one dependency
+    per level) swept as one part gives the in-part hop t_local; with its rows alternating between
+    two parts every dependency crosses, which gives the cross-part hop t_cross.  A sweep of
+    `levels` levels whose chain crosses `crossings` part boundaries cannot finish in less than
+    (levels - crossings) t_local + crossings t_cross.  Kernel-only times (library event profile)."""
+    rp_d, ci_d, v_d = (torch.as_tensor(a, device=device) for a in chain_csr(n))
     lv = hec.sptrsv_analyze(rp_d, ci_d, 0)
     plan = hec.sptrsv_plan_create(hec.hec_from_csr(rp_d, ci_d, v_d, levels=lv, vdt=vdt), lv)
     b = torch.ones(n, dtype=torch.float64, device=device)

@@ -1,0 +1,59 @@
+"""Host logic of bench.py (no GPU): the algorithmic byte count of a sweep against the printed
+per-application totals for the 128^3 ILU(0) factors, the pencil grid of the partitioned schedule,
+the empty-level chain of the latency floor, and the traffic figure read from a committed capture."""
+import os
+import sys
+
+import numpy as np
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+N128 = 128 ** 3
+NNZ_L_128 = 8_339_456  # ILU(0) of the 7-point matrix on 128^3, diagonal included (= nnz of U)
+
+
+def test_sweep_bytes_match_the_printed_totals():
+    # one L+U application: 250.9 MB with FP32 values, 317.6 MB with FP64, 1.26 GB for 16 columns
+    lu = lambda sv, k: 2 * bench.sweep_bytes(NNZ_L_128, N128, k, sv)
+    assert round(lu(4, 1) / 1e6, 1) == 250.9
+    assert round(lu(8, 1) / 1e6, 1) == 317.6
+    assert round(lu(4, 16) / 1e9, 2) == 1.26
+    # the terms: values + indices, tail pointers, FP64 b read and x write, two index reads
+    assert bench.sweep_bytes(10, 4, 1, 8) == 10 * 12 + 4 * 5 + 2 * 4 * 8 + 2 * 4 * 4
+
+
+def test_sweep_grid_parts_fit():
+    from paper_1606_00541_gb300 import synth
+    for m, parts, crossings in ((128, 144, 22), (200, 152, 25)):
+        nb = bench.sweep_grid(m)
+        part, nparts = synth.grid_boxes(m, nb)
+        assert nparts == parts and sum(k - 1 for k in nb) == crossings
+        # every part is an x-pencil whose FP32 solution fits the 227 KB of shared memory a block has
+        sizes = np.bincount(part, minlength=nparts)
+        assert sizes.min() > 0 and sizes.max() * 4 <= 227 * 1024
+        g = np.arange(m ** 3)
+        y, z = (g // m) % m, g // (m * m)
+        assert np.all(part == (y * nb[1]) // m + nb[1] * ((z * nb[2]) // m))
+
+
+def test_chain_has_one_row_and_one_dependency_per_level():
+    n = 64
+    rp, ci, v = bench.chain_csr(n)
+    assert oracle.check_triangular((rp, ci, v), 0) == 0
+    lev, nlev = oracle.levels((rp, ci, v), 0)
+    assert nlev == n and np.array_equal(lev, np.arange(n))
+    assert np.array_equal(np.diff(rp), np.r_[1, np.full(n - 1, 2)])
+    # well conditioned: for b = 1, x_i = 1 + x_{i-1} / 2, i.e. x_i = 2 - 2^-i
+    x = oracle.lower_solve((rp, ci, v), np.ones(n))
+    assert np.abs(x - (2.0 - 0.5 ** np.arange(n))).max() <= 4e-16
+
+
+def test_recorded_traffic_follows_the_source_digest(monkeypatch):
+    t = bench.recorded_traffic("part")
+    assert t is not None and 5e7 < t < 2e8  # the committed capture matches the committed sources
+    monkeypatch.setattr(bench, "sweep_source_digest", lambda: "0" * 16)
+    assert bench.recorded_traffic("part") is None and bench.recorded_traffic("global") is None
