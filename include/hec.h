@@ -205,8 +205,9 @@ hec_status sptrsv_upper(const sptrsv_plan* p, int nrhs, const double* b, int ldb
  * threads: 128, 256, 512 or 1024 (0 = 256) per block; the part's level is worked by all the
  * block's warps, so large parts want 1024.  Applies to single-right-hand-side sweeps of this
  * plan (sptrsv_lower / sptrsv_upper / ilu_apply with nrhs = 1); nparts = 0 removes it.  The plan
- * keeps its own copy of the factor in the partitioned order, and an n-entry buffer into which
- * each sweep first gathers its right-hand side in that order.  Synchronizes `stream`. */
+ * keeps its own copy of the factor in the partitioned order and, for FP32 or BF16 values, an
+ * n-entry buffer into which each sweep first gathers its right-hand side in that order.
+ * Synchronizes `stream`. */
 hec_status sptrsv_plan_partition(sptrsv_plan* p, const int* part, int nparts, int threads,
                                  void* stream);
 int sptrsv_partition_capacity(const sptrsv_plan* p, int threads);

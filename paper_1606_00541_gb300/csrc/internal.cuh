@@ -104,7 +104,7 @@ struct hec_part_data {
     int* tcol = nullptr;
     void* tval = nullptr;
     void* dinv = nullptr;
-    void* bp = nullptr;         // [n] right-hand side of the current sweep in plan order (work type)
+    void* bp = nullptr;         // [n] right-hand side of the current sweep in plan order (FP32 work only)
     int* part_chunk = nullptr;  // [nparts+1] first level-aligned chunk of each part
     int2* chunks = nullptr;     // (first plan row, rows <= 32)
     int nchunks = 0;

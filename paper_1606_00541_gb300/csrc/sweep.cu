@@ -745,7 +745,12 @@ struct PartRow {
         if (have && lane < ch.y) {
             const int r = ch.x + lane;
             g = __ldg(p.rowg + r);
-            b = __ldg((const AT*)p.bp + r);
+            if (sizeof(AT) == 4) {
+                b = __ldg((const AT*)p.bp + r);
+            } else {  // FP64: gathered here (the row is loaded when its chunk starts)
+                const int gr = p.gather ? __ldg(p.gather + g) : g;
+                b = (AT)__ldg(p.b + (long)gr * p.ldb);
+            }
             t0 = __ldg(p.tptr + r);
             t1 = __ldg(p.tptr + r + 1);
             d = __ldg((const XT*)p.dinv + r);
@@ -784,7 +789,11 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_part(PartParams p) {
     // slab slots carried in the prefetched row: all four of a narrow FP32 slab, fewer where the
     // registers of a 1024-thread block (64 a thread) would otherwise spill
     constexpr int NP = WMAX > 4 ? 0 : sizeof(AT) == 8 ? 2 : WMAX;
-    constexpr bool PF = WMAX <= 4 || sizeof(AT) == 4;  // FP64 with a wide slab loads at the chunk
+    // FP32 work: the next chunk's row is loaded while the current one waits, and the right-hand
+    // side comes gathered by k_part_prep.  FP64 work: a level is long enough (FP64 arithmetic on
+    // the chain) that loading the row, right-hand side gather included, when the chunk starts
+    // costs nothing, while a gathering pass before the sweep would.
+    constexpr bool PF = sizeof(AT) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WT* sxp = (WT*)smem_raw;
     const unsigned int sbase = (unsigned int)__cvta_generic_to_shared(smem_raw);
@@ -1097,8 +1106,11 @@ hec_status launch_part(const sptrsv_plan* pl, PartParams& pp, cudaStream_t s) {
     const int fb = (int)std::min(4096L, std::max(1L, (count + 255) / 256));
     {
         ProfScope ps_(s, PROF_FILL);
-        k_part_prep<XT><<<fb, 256, 0, s>>>((int)count, (XT*)pp.xp, P->rowg, pp.gather, pp.b, pp.ldb,
-                                           (typename Acc<XT>::T*)P->bp);
+        if (sizeof(typename Acc<XT>::T) == 4)
+            k_part_prep<XT><<<fb, 256, 0, s>>>((int)count, (XT*)pp.xp, P->rowg, pp.gather, pp.b, pp.ldb,
+                                               (typename Acc<XT>::T*)P->bp);
+        else
+            k_fill_sentinel<XT><<<fb, 256, 0, s>>>((XT*)pp.xp, count);
     }
     HEC_LAUNCHED();
     void* args[] = {&pp};
@@ -1400,7 +1412,7 @@ hec_status build_partition(sptrsv_plan* p, const int* part, int nparts, cudaStre
     const size_t ws = T->vdt == HEC_F64 ? 8 : 4;
     if ((st = dalloc(&P->ell_col, (size_t)T->w * T->ld)) || (st = dmalloc(&P->ell_val, vs * (size_t)T->w * T->ld + 16)) ||
         (st = dalloc(&P->tcol, (size_t)T->tail_nnz)) || (st = dmalloc(&P->tval, vs * (size_t)T->tail_nnz + 16)) ||
-        (st = dmalloc(&P->dinv, ws * (size_t)n + 16)) || (st = dmalloc(&P->bp, ws * (size_t)n + 16)))
+        (st = dmalloc(&P->dinv, ws * (size_t)n + 16)) || (ws == 4 && (st = dmalloc(&P->bp, ws * (size_t)n + 16))))
         return done(st);
     const int gl = (T->ld + 255) / 256;
     if (T->vdt == HEC_F64) {

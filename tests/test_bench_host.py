@@ -52,8 +52,11 @@ def test_chain_has_one_row_and_one_dependency_per_level():
     assert np.abs(x - (2.0 - 0.5 ** np.arange(n))).max() <= 4e-16
 
 
-def test_recorded_traffic_follows_the_source_digest(monkeypatch):
-    t = bench.recorded_traffic("part")
-    assert t is not None and 5e7 < t < 2e8  # the committed capture matches the committed sources
+def test_recorded_traffic_follows_the_source_digest(monkeypatch, tmp_path):
+    cap = tmp_path / "capture.md"
+    cap.write_text("notes\n\ntraffic_bytes_per_launch: 107734400 source_digest: %s\n" % bench.sweep_source_digest())
+    monkeypatch.setattr(bench, "SWEEP_PROFILES", {"part": str(cap), "global": str(tmp_path / "missing.md")})
+    assert bench.recorded_traffic("part") == 107734400
+    assert bench.recorded_traffic("global") is None  # no capture
     monkeypatch.setattr(bench, "sweep_source_digest", lambda: "0" * 16)
-    assert bench.recorded_traffic("part") is None and bench.recorded_traffic("global") is None
+    assert bench.recorded_traffic("part") is None  # sources changed since the capture
