@@ -62,10 +62,11 @@ const char* hec_last_error(void);
 int hec_version(void);
 long long hec_launch_count(void);
 
-/* Kernel timing for measurement: while enabled, every triangular-sweep launch is bracketed by a
- * pair of CUDA events recorded on the stream it is launched on.  hec_profile_read waits for the
- * recorded events and returns the summed device time (ms) and the number of sweep launches
- * since the last reset (reset != 0 clears the record).  Off by default. */
+/* Kernel timing for measurement: while enabled, every launch of the library's kernel categories
+ * (listed at hec_profile_read_category) is bracketed by a pair of CUDA events recorded on the
+ * stream it is launched on.  hec_profile_read waits for the recorded events and returns the
+ * summed device time (ms) and the number of triangular-sweep launches since the last reset
+ * (reset != 0 clears the whole record).  Off by default. */
 hec_status hec_profile_enable(int on);
 /* Enables the record for the categories in `mask` only (bit c = category c of
  * hec_profile_read_category; 0 disables), so a timed run can bracket just the kernels it reports
@@ -74,7 +75,8 @@ hec_status hec_profile_enable(int on);
 hec_status hec_profile_enable_categories(unsigned int mask);
 hec_status hec_profile_read(double* sweep_ms, long long* sweep_launches, int reset);
 /* The same record for other kernel classes (not reset): 0 sweeps, 1 SpMV, 2 Gram-Schmidt dots
- * and updates, 3 the small Arnoldi kernels, 4 vector scale/copy/update, 5 sentinel fills. */
+ * and updates, 3 the small Arnoldi kernels, 4 vector scale/copy/update, 5 sentinel fills (with
+ * the partitioned sweep's right-hand-side gather). */
 hec_status hec_profile_read_category(int category, double* ms, long long* launches);
 
 /* ---------------------------------------------------------------------------------------- */
