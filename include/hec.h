@@ -422,12 +422,25 @@ hec_status hec_ras_destroy(hec_ras* R);
  * (chunk table, level-ordered solution, status word) lives in one static device buffer of
  * sptrsv_noalloc_capacity() bytes (32 MiB), which every GPU that loads the library holds until
  * the process exits.  The caller still passes tri and lv (built once with sptrsv_analyze and
- * hec_from_csr) and the device arrays b and x, with the layout of sptrsv_lower.
- *   - Size limit: a problem whose scratch (n * (nrhs + 1) * 8 bytes for FP64 factors, 4 for
- *     FP32 / BF16, plus the chunk table) exceeds the buffer is rejected with HEC_ERR_INVALID_ARG and a
- *     message giving the bytes needed; use sptrsv_lower / sptrsv_upper for those.
- *   - The first call on a device looks up the buffer's device address (cudaGetSymbolAddress)
- *     with that device current; make that first call before any stream capture.
+ * hec_from_csr) and the device arrays b and x, with the layout of sptrsv_lower.  The lane
+ * layout is that of a plan with default settings (for one right-hand side the lanes-per-row rule
+ * of hec_tune.lanes_per_row = 0), so the results equal those of sptrsv_lower / sptrsv_upper on a
+ * default plan bit for bit.
+ *   - Size limit: the scratch of a problem is, in bytes, with ws = 8 for FP64 factors and 4 for
+ *     FP32 / BF16, kp = nrhs rounded up to a power of two, and rpw = 32 / (lanes per row) rows per
+ *     chunk (32 for one right-hand side with one lane per row):
+ *       256 + a(4 (nlev + 1)) + a(8 (nlev + ceil(n / rpw))) + a(ws n kp) + a(ws n),
+ *     where a() rounds up to a multiple of 256 (status word, chunk prefix, chunk table,
+ *     level-ordered solution, reciprocal diagonal).  A problem beyond the buffer is rejected with
+ *     HEC_ERR_INVALID_ARG and a message giving the bytes needed; use sptrsv_lower / sptrsv_upper
+ *     for those.
+ *   - The buffer belongs to the library's device code.  With lazy module loading (the CUDA
+ *     default) the device reserves it at the first call on that device (any size, n = 0
+ *     included), not when the library is loaded: a caller that must see no change in free device
+ *     memory after initialization makes one warm-up call then.  Later calls change nothing.
+ *   - Every call looks up the buffer's device address (cudaGetSymbolAddress, which allocates
+ *     nothing) with the calling device current; make the first call on a device before any
+ *     stream capture.
  *   - All calls share the one buffer and it keeps the last call's contents; every call resets
  *     the parts that must start fresh.  Calls whose work overlaps on the GPU (different
  *     streams, or different host threads on one device) race on the buffer: serialize them.

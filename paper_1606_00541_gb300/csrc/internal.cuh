@@ -169,6 +169,14 @@ inline int log2i(int v) {
     while ((1 << l) < v) ++l;
     return l;
 }
+// Single-right-hand-side lanes per row by row length: the one-lane kernel polls up to 8 slab
+// slots and 4 tail entries per wait and waits again for every further slot; several lanes per
+// row poll 3 slab slots and 2 tail entries each, all in one wait.
+inline int default_lanes_per_row(const hec_matrix* T) {
+    const long long over = T->tail_nnz - (long long)T->n;  // tail entries besides the diagonals
+    if (T->w <= 8 && over * 2 <= (long long)T->n) return 1;
+    return T->w <= 6 ? 2 : T->w <= 12 ? 4 : 8;
+}
 
 // sweep launcher shared by sptrsv_* and ilu_apply: gather[r] is the row of b feeding new row r
 // (NULL = identity), scatter[r] the row of x receiving it (NULL = identity, -1 = skip).

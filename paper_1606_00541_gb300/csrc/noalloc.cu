@@ -10,9 +10,16 @@
 // where a cudaMalloc (which may synchronize the device) is unacceptable.
 //
 // Host code never dereferences g_noalloc_scratch: in host code the symbol is only a stand-in,
-// so its device address is looked up once per device with cudaGetSymbolAddress and cached.
+// so every call looks up its device address with cudaGetSymbolAddress, with the calling device
+// current.  The lookup allocates nothing and is cheap; doing it on every call (instead of caching
+// the address per device) keeps the call correct after the context is reset and recreated.
+//
+// The buffer is part of this library's device code module.  With lazy module loading (the CUDA
+// default) that module is loaded, and the buffer reserved, at the first use of a kernel or symbol
+// of this file on a device, i.e. during the first call of sptrsv_solve_noalloc there (of any size,
+// n = 0 included).  Callers that must not see device memory change inside later calls make one
+// warm-up call at initialization.
 #include <algorithm>
-#include <mutex>
 #include <string>
 
 #include "internal.cuh"
@@ -22,10 +29,6 @@ namespace {
 
 constexpr size_t kScratchBytes = size_t(32) << 20;  // 32 MiB, held by every device that loads the library
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_na_mu;
-void* g_na_ptr[kMaxDevices] = {};
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -106,17 +109,10 @@ __global__ void k_na_dinv<__nv_bfloat16, float>(int n, const int* __restrict__ t
 }
 
 hec_status scratch_ptr(unsigned char** out) {
-    int dev = 0;
-    HEC_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return set_error(HEC_ERR_INVALID_ARG, "sptrsv_solve_noalloc: device ordinal too large");
-    std::lock_guard<std::mutex> g(g_na_mu);
-    if (!g_na_ptr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return cuda_error(e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
-        g_na_ptr[dev] = p;
-    }
-    *out = (unsigned char*)g_na_ptr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_error(e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
+    *out = (unsigned char*)p;
     return HEC_OK;
 }
 
@@ -135,10 +131,15 @@ HEC_API hec_status sptrsv_solve_noalloc(const hec_matrix* tri, const hec_levels*
         return set_error(HEC_ERR_INVALID_ARG, "sptrsv_solve_noalloc: need a triangular HEC matrix, the analysis it "
                                               "was packed with, 1 <= nrhs <= 16 and ld >= nrhs");
     if (status_out) *status_out = 0;
+    unsigned char* base = nullptr;
+    HEC_CHECK(scratch_ptr(&base));  // also loads the buffer on a device's first call
     const int n = tri->n, nlev = lv->nlev;
     if (n == 0) return HEC_OK;
-    const int kp = sweep_kp(nrhs);                        // padded row stride of the solution
-    const int kp_idx = log2i(sweep_lpr(nrhs, tri->vdt));  // lane layout -> chunk table
+    const int kp = sweep_kp(nrhs);  // padded row stride of the solution
+    // lane layout (as a plan with default settings): one right-hand side takes the lanes-per-row
+    // rule of the row lengths, more take G right-hand sides per lane; it selects the chunk table
+    const int lpr1 = nrhs == 1 ? default_lanes_per_row(tri) : 1;
+    const int kp_idx = log2i(nrhs == 1 ? lpr1 : sweep_lpr(nrhs, tri->vdt));
     const int rpw = 32 >> kp_idx;
     // layout: [status | chunk prefix (nlev+1) | chunk table | level-ordered solution]
     const size_t chunk_cap = (size_t)nlev + ((size_t)n + rpw - 1) / rpw;
@@ -153,8 +154,6 @@ HEC_API hec_status sptrsv_solve_noalloc(const hec_matrix* tri, const hec_levels*
         return set_error(HEC_ERR_INVALID_ARG,
                          "sptrsv_solve_noalloc: problem needs " + std::to_string(need) + " bytes of scratch, more than the " +
                              std::to_string(kScratchBytes) + "-byte static buffer (use sptrsv_lower/sptrsv_upper)");
-    unsigned char* base = nullptr;
-    HEC_CHECK(scratch_ptr(&base));
     cudaStream_t s = S(stream);
     int* status = (int*)base;
     int* cptr = (int*)(base + off_cptr);
@@ -186,6 +185,7 @@ HEC_API hec_status sptrsv_solve_noalloc(const hec_matrix* tri, const hec_levels*
     plan.chunks[kp_idx] = tbl;
     plan.nchunks[kp_idx] = (int)chunk_cap;
     plan.dinv = dinv;
+    plan.lpr1 = lpr1;
     hec_status st = sweep(&plan, nrhs, b, ldb, lv->iperm, x, ldx, lv->iperm, s);
     if (st != HEC_OK) return st;
     if (status_out) {

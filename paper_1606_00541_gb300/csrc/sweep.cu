@@ -1475,12 +1475,7 @@ HEC_API hec_status sptrsv_plan_create(const hec_matrix* tri, const hec_levels* l
         if (tune->debug_unpublished_row > 0) p->skip_row = tune->debug_unpublished_row - 1;
         if (tune->backoff_ns > 0) p->backoff_ns = tune->backoff_ns;
     }
-    // single-RHS lanes per row by row length: the one-lane kernel polls up to 8 slab slots and 4
-    // tail entries per wait and waits again for every further slot; several lanes per row poll
-    // 3 slab slots and 2 tail entries each, all in one wait
-    const long long over = tri->tail_nnz - (long long)tri->n;  // tail entries besides the diagonals
-    if (tri->w <= 8 && over * 2 <= (long long)tri->n) p->lpr1 = 1;
-    else p->lpr1 = tri->w <= 6 ? 2 : tri->w <= 12 ? 4 : 8;
+    p->lpr1 = default_lanes_per_row(tri);
     if (tune && tune->lanes_per_row) p->lpr1 = tune->lanes_per_row;
     if (p->lpr1 != 1 && p->lpr1 != 2 && p->lpr1 != 4 && p->lpr1 != 8) {
         delete p;
