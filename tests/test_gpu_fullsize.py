@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 import torch
 
+import _bounds
 import oracle
 from paper_1606_00541_gb300 import synth
 
@@ -86,6 +87,53 @@ def test_cfg1_fgmres_fp32_factors(hec, cfg1):
     z = oracle.ilu_apply(L, U, b)
     zg = s.apply(dev(b)).cpu().numpy()
     assert relmax(zg, z) <= 1e-5  # FP32 factor values: one apply within FP32-level error
+
+
+@pytest.mark.parametrize("vdt", ["f32", "bf16"])
+def test_cfg1_timed_partitioned_sweeps_against_oracle(hec, cfg1, vdt):
+    """The exact form bench.py times: FP32 (and BF16) factor values, the single-right-hand-side
+    partitioned kernel on 144 x-pencils of the 128^3 grid with one 1024-thread block each.  The
+    lower and upper sweeps and the ILU apply are compared element by element with the oracle's
+    FP64 substitution on the same rounded values, under the componentwise FP32 bound
+    gamma_{q+2}(u32) M(T)^-1 |T| |x| with a safety factor of 4; the error against the unrounded
+    FP64 solve is printed.  The factors are the oracle's ILU(0) (the GPU factorization equals it
+    to 1e-12, tested above), so no input of the reference comes from the GPU."""
+    m, A, L, U = cfg1
+    n = m ** 3
+    part, nparts = synth.grid_boxes(m, (1, 12, 12))
+    assert nparts == 144
+    b = synth.uniform_vector(n, 1)
+    xs = {}
+    for uplo, T in [(0, L), (1, U)]:
+        Td = [dev(a) for a in T]
+        lv = hec.sptrsv_analyze(Td[0], Td[1], uplo)
+        H = hec.hec_from_csr(*Td, levels=lv, vdt=vdt)
+        p = hec.sptrsv_plan_create(H, lv, 1)
+        hec.sptrsv_plan_partition(p, dev(part), nparts, 1024)
+        f = hec.sptrsv_lower if uplo == 0 else hec.sptrsv_upper
+        x = f(p, dev(b)).cpu().numpy()
+        assert hec.hec_sync_status(p) == 0
+        Tr = _bounds.rounded(T, vdt)
+        xr = (oracle.lower_solve if uplo == 0 else oracle.upper_solve)(Tr, b)
+        bound = _bounds.sweep_bound(Tr, uplo, xr)
+        ratio = float(np.max(np.abs(x - xr) / (bound + 1e-300)))
+        assert ratio <= 4.0, (uplo, ratio)
+        x64 = (oracle.lower_solve if uplo == 0 else oracle.upper_solve)(T, b)
+        xs[uplo] = (x, xr)
+        print("cfg1 %s uplo %d: err/bound %.3f, rel err vs rounded-value fp64 %.3e, vs unrounded fp64 %.3e"
+              % (vdt, uplo, ratio, relmax(x, xr), relmax(x, x64)))
+    # the ILU apply in the solver's configuration (both plans partitioned, the intermediate kept in
+    # the upper factor's order)
+    s = hec.IluSolver([dev(a) for a in L], [dev(a) for a in U], vdt=vdt)
+    s.partition(dev(part), nparts, threads=1024)
+    z = s.apply(dev(b)).cpu().numpy()
+    Lr, Ur = _bounds.rounded(L, vdt), _bounds.rounded(U, vdt)
+    y = oracle.lower_solve(Lr, b)
+    zr = oracle.upper_solve(Ur, y)
+    bound = _bounds.apply_bound(Lr, Ur, y, zr)
+    ratio = float(np.max(np.abs(z - zr) / (bound + 1e-300)))
+    assert ratio <= 4.0, ratio
+    print("cfg1 %s ilu apply: err/bound %.3f, rel err %.3e" % (vdt, ratio, relmax(z, zr)))
 
 
 def test_cfg2_ilut_27pt_sweeps_1_and_16_rhs(hec):

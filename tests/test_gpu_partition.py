@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 import torch
 
+import _bounds
 import oracle
 from paper_1606_00541_gb300 import synth
 
@@ -63,15 +64,10 @@ def test_partitioned_sweep_fp64_parity(hec, kind, scheme, uplo, threads):
     p = plans(hec, T, uplo)
     if scheme == "box" and box is None:
         pytest.skip("no grid partition for this matrix")
-    if scheme == "contiguous":
-        hec.sptrsv_plan_partition(p, None, 37, threads)
-    elif scheme == "box":
-        hec.sptrsv_plan_partition(p, dev(box), int(box.max()) + 1, threads)
-    elif scheme == "scattered":
-        part = np.random.default_rng(7).integers(0, 23, size=n).astype(np.int32)
-        hec.sptrsv_plan_partition(p, dev(part), 23, threads)
-    else:
+    if scheme == "single":
         hec.sptrsv_plan_partition(p, None, 1, threads)
+    else:
+        _partition(hec, p, scheme, n, box, threads)
     b = synth.uniform_vector(n, 12)
     x = (hec.sptrsv_lower if uplo == 0 else hec.sptrsv_upper)(p, dev(b)).cpu().numpy()
     ref = (oracle.lower_solve if uplo == 0 else oracle.upper_solve)(T, b)
@@ -79,20 +75,59 @@ def test_partitioned_sweep_fp64_parity(hec, kind, scheme, uplo, threads):
     assert hec.hec_sync_status(p) == 0
 
 
+def _partition(hec, p, scheme, n, box, threads):
+    if scheme == "contiguous":
+        hec.sptrsv_plan_partition(p, None, 37, threads)
+    elif scheme == "box":
+        hec.sptrsv_plan_partition(p, dev(box), int(box.max()) + 1, threads)
+    else:
+        part = np.random.default_rng(7).integers(0, 23, size=n).astype(np.int32)
+        hec.sptrsv_plan_partition(p, dev(part), 23, threads)
+
+
+@pytest.mark.parametrize("kind", ["fv7", "fv7_ilu1", "27pt_ilut"])
+@pytest.mark.parametrize("scheme", ["contiguous", "box", "scattered"])
+@pytest.mark.parametrize("threads", [256, 1024])
 @pytest.mark.parametrize("vdt", ["f32", "bf16"])
-def test_partitioned_reduced_precision_close(hec, vdt):
-    A, (L, U), box = factors("fv7")
+def test_partitioned_reduced_precision_against_oracle(hec, kind, scheme, threads, vdt):
+    """The partitioned kernel as the solver runs it with FP32 / BF16 values (the next chunk's row
+    prefetched while the current one waits, the right-hand side gathered into plan order in FP32
+    before the sweep) against the oracle's FP64 substitution with the same rounded values, under
+    the componentwise bound gamma_{q+2}(u32) M(T)^-1 |T| |x| (safety factor 4), for the lower and
+    the upper factor; the error against the unrounded FP64 solve is printed."""
+    A, (L, U), box = factors(kind)
     n = len(A[0]) - 1
     b = synth.uniform_vector(n, 3)
     for uplo, T in [(0, L), (1, U)]:
-        p0 = plans(hec, T, uplo, vdt)
-        p1 = plans(hec, T, uplo, vdt)
-        hec.sptrsv_plan_partition(p1, dev(box), int(box.max()) + 1)
+        p = plans(hec, T, uplo, vdt)
+        _partition(hec, p, scheme, n, box, threads)
         f = hec.sptrsv_lower if uplo == 0 else hec.sptrsv_upper
-        x0 = f(p0, dev(b)).cpu().numpy()
-        x1 = f(p1, dev(b)).cpu().numpy()
-        # same rounded values, FP32 sums in another order
-        assert relmax(x1, x0) <= 1e-5
+        x = f(p, dev(b)).cpu().numpy()
+        assert hec.hec_sync_status(p) == 0
+        Tr = _bounds.rounded(T, vdt)
+        xr = (oracle.lower_solve if uplo == 0 else oracle.upper_solve)(Tr, b)
+        bound = _bounds.sweep_bound(Tr, uplo, xr)
+        assert np.all(np.abs(x - xr) <= 4 * bound + 1e-300), float(np.max(np.abs(x - xr) / (bound + 1e-300)))
+        x64 = (oracle.lower_solve if uplo == 0 else oracle.upper_solve)(T, b)
+        print(kind, scheme, threads, vdt, uplo, "err/bound %.3f, err vs unrounded fp64 %.3e"
+              % (float(np.max(np.abs(x - xr) / (bound + 1e-300))), relmax(x, x64)))
+
+
+@pytest.mark.parametrize("vdt", ["f32", "bf16"])
+def test_partitioned_reduced_precision_ilu_apply_against_oracle(hec, vdt):
+    """The ILU apply with both factors partitioned on grid boxes at 1024 threads (the solver's
+    single-right-hand-side path) against the oracle's z = U^-1 L^-1 r with the rounded values."""
+    A, (L, U), box = factors("fv7")
+    n = len(A[0]) - 1
+    s = hec.IluSolver([dev(a) for a in L], [dev(a) for a in U], vdt=vdt)
+    s.partition(dev(box), int(box.max()) + 1, threads=1024)
+    r = synth.uniform_vector(n, 17)
+    z = s.apply(dev(r)).cpu().numpy()
+    Lr, Ur = _bounds.rounded(L, vdt), _bounds.rounded(U, vdt)
+    y = oracle.lower_solve(Lr, r)
+    zr = oracle.upper_solve(Ur, y)
+    bound = _bounds.apply_bound(Lr, Ur, y, zr)
+    assert np.all(np.abs(z - zr) <= 4 * bound + 1e-300)
 
 
 def test_partitioned_ilu_fgmres(hec):
