@@ -1,7 +1,7 @@
 """CPU oracle for the level-scheduled HEC triangular solver (arXiv 1606.00541).
 
 TEST INFRASTRUCTURE ONLY: plain serial FP64 code on CSR matrices (``hec_oracle.c`` plus the
-conv3d reference in ``conv_ref.py``).  Only the tests, ``__graft_entry__.smoke()`` and the CPU
+conv3d reference in ``conv_ref.py`` and the learned stage's gated step in ``stage_ref.py``).  Only the tests, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` may import it.  It shares no code with the CUDA library and does not
 import the product package.
 
