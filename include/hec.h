@@ -265,13 +265,18 @@ typedef struct {
 } hec_fgmres_info;
 
 /* Solves A x = b by right-preconditioned flexible GMRES(restart), z_j = M^-1 v_j with the ILU
- * or RAS preconditioner M (NULL = none), FP64 throughout: SpMV, classical Gram-Schmidt with one
- * re-orthogonalization, Givens rotations.  Each of the nrhs right-hand sides (row-major n x
- * nrhs, nrhs <= 16) has its own Krylov space; their kernels run batched.  x holds x0 on entry
- * (zero it for x0 = 0) and the solution on exit.  Convergence: the Arnoldi estimate
- * |g_{j+1}| <= rtol ||b|| ends a cycle, then the true residual is checked; max_iters bounds the
- * inner iterations.  info (host, may be NULL) receives the statistics.  Synchronizes `stream`
- * once per inner iteration (the Hessenberg column is solved on the host).  Returns
+ * or RAS preconditioner M (NULL = none), FP64 throughout: SpMV, modified Gram-Schmidt (one
+ * persistent kernel per inner iteration, a fixed-order grid-wide reduction per projection),
+ * Givens rotations.  Each of the nrhs right-hand sides (row-major n x nrhs, nrhs <= 16) has its
+ * own Krylov space; their kernels run batched.  x holds x0 on entry (zero it for x0 = 0) and the
+ * solution on exit.  Convergence: the Arnoldi estimate |g_{j+1}| <= rtol ||b|| ends a cycle,
+ * then the true residual ||b - A x|| is computed and checked; max_iters bounds the inner
+ * iterations.  info (host, may be NULL) receives the statistics.
+ * Synchronization: the Hessenberg matrix, the rotations and the residual estimate stay on the
+ * device.  Inside a restart cycle the host only reads a per-iteration "still active" flag through
+ * pinned memory one iteration behind the device (an event wait, the device never idles for the
+ * host); `stream` is synchronized at each restart (true residual, status of the sweeps) and at
+ * exit.  Allocates its workspace (restart + 1 + restart vectors of n x nrhs) per call.  Returns
  * HEC_ERR_NOT_CONVERGED when max_iters is reached, HEC_ERR_TIMEOUT when a sweep's dependency
  * wait timed out. */
 typedef struct hec_stage hec_stage;
@@ -315,6 +320,16 @@ hec_status net_forward(hec_net* net, int nx, int ny, int nz, int zs, const void*
 hec_status net_train_step(hec_net* net, int nx, int ny, int nz, int zs, const void* x_in,
                           const float* target, float lr, int update, float* loss_out,
                           void* stream);
+/* The two halves of net_train_step.  net_backward: forward, mean-squared error against target
+ * and backward on one minibatch (layout as net_forward); the parameter gradients are kept in the
+ * net (net_get_params) and loss_out (host, may be NULL) receives the loss, after which the call
+ * synchronizes `stream`.  net_adam_step: one Adam step (beta 0.9 / 0.999, eps 1e-8,
+ * bias-corrected with the net's own step count) from the kept gradients with rate lr, then the
+ * BF16 weight copies the forward pass uses.  net_train_step(..., update = 1) = net_backward +
+ * net_adam_step. */
+hec_status net_backward(hec_net* net, int nx, int ny, int nz, int zs, const void* x_in,
+                        const float* target, float* loss_out, void* stream);
+hec_status net_adam_step(hec_net* net, float lr, void* stream);
 
 /* A training sample from one residual / error pair on an n-voxel field: sigma = RMS(r) (device
  * FP64, *sigma_out), x_out = channels-last BF16 [n][16] with channel 0 = r / sigma, channel 1 =
@@ -358,6 +373,27 @@ hec_status hec_csr_destroy(hec_csr* M);
  * the triangular solver, Sec. 1).  Synchronizes `stream`. */
 hec_status csr_triangle(int n, const int* rowptr, const int* col, const double* val, int uplo,
                         int strict, hec_csr** out, void* stream);
+/* Symmetric Gauss-Seidel smoother on the level-scheduled sweeps (the smoothers the paper names as
+ * another use of the triangular solver, Sec. 1).  With A = L_s + D + U_s (strict lower part,
+ * diagonal, strict upper part of the n x n CSR matrix, ascending columns, nonzero diagonal), one
+ * symmetric sweep is the forward sweep (D + L_s) x' = b - U_s x followed by the backward sweep
+ * (D + U_s) x'' = b - L_s x'; each triangle is solved by the HEC sweep of Alg. 2 (level
+ * scheduling reorders only independent rows, so a sweep equals sequential Gauss-Seidel up to
+ * rounding).  sgs_create builds the handle: the triangles D + L_s and D + U_s analysed, packed
+ * with values of type vdt and planned for up to max_nrhs (<= 16) right-hand sides; U_s and L_s
+ * in FP64 for the residual products; one n x max_nrhs work vector.  Synchronizes `stream`.
+ * sgs_smooth runs `sweeps` symmetric sweeps on x in place (row-major n x nrhs FP64; x holds the
+ * start on entry and the result on exit; b is not modified).  Asynchronous on `stream`;
+ * sgs_sync_status reads and clears the device status of the two sweeps (HEC_ERR_TIMEOUT when a
+ * dependency wait ran out). */
+typedef struct hec_sgs hec_sgs;
+hec_status sgs_create(int n, const int* rowptr, const int* col, const double* val, hec_dtype vdt,
+                      int max_nrhs, hec_sgs** out, void* stream);
+hec_status sgs_smooth(const hec_sgs* sgs, int nrhs, const double* b, int ldb, double* x, int ldx,
+                      int sweeps, void* stream);
+hec_status sgs_sync_status(const hec_sgs* sgs, void* stream);
+hec_status sgs_destroy(hec_sgs* sgs);
+
 /* ILU(k) for k = 0 (pattern of A) or k = 1 (pattern of A plus the fill of level 1: entries
  * (i, j) reached by i -> q -> j with q < min(i, j) both original entries).  Each row i is
  * eliminated IKJ-style: for the pattern columns q < i in ascending order,

@@ -9,8 +9,9 @@
 //
 // Convolution = implicit GEMM: for each of the 27 taps, D[voxels x 16 out] += X_shifted[voxels x
 // 16 in] * W_tap[16 in x 16 out], one mma.sync.m16n8k16 (BF16 in, FP32 accumulate) per 16
-// voxels per 8 output channels per tap.  A block computes a 32 x 4 x 1 voxel tile from a 34 x 6 x 3
-// halo tile staged in shared memory together with all 27 weight taps.  The data gradient is the
+// voxels per 8 output channels per tap.  A forward block computes a 32 x 4 x 4 voxel tile from a
+// 34 x 6 x 6 halo tile staged in shared memory together with all 27 weight taps (the weight-gradient
+// kernel works on 32 x 4 x 1 tiles with a 34 x 6 x 3 halo).  The data gradient is the
 // same kernel run with the spatially flipped, channel-transposed weights and the ReLU mask of
 // the layer applied while the halo is staged; the weight gradient is a GEMM over voxels with
 // per-block partial sums reduced in a fixed order (deterministic).
@@ -704,13 +705,12 @@ HEC_API hec_status net_forward(hec_net* N, int nx, int ny, int nz, int zs, const
     return HEC_OK;
 }
 
-HEC_API hec_status net_train_step(hec_net* N, int nx, int ny, int nz, int zs, const void* x_in, const float* target,
-                                  float lr, int update, float* loss_out, void* stream) {
-    clear_error();
-    if (!N || !x_in || !target) return set_error(HEC_ERR_INVALID_ARG, "net_train_step: NULL");
+// forward, loss and backward on one minibatch; the gradients stay in N->G
+static hec_status net_backward_impl(hec_net* N, int nx, int ny, int nz, int zs, const void* x_in, const float* target,
+                                    float* loss_out, cudaStream_t s, const char* who) {
+    if (!N || !x_in || !target) return set_error(HEC_ERR_INVALID_ARG, std::string(who) + ": NULL");
     Geom g{nx, ny, nz, zs};
     HEC_CHECK(check_geom(g));
-    cudaStream_t s = S(stream);
     const long nvox = (long)nx * ny * nz;
     const dim3 grid = conv_grid(g);
     HEC_CHECK(ensure(N, nvox, (long)grid.x * grid.y * grid.z));
@@ -721,14 +721,6 @@ HEC_API hec_status net_train_step(hec_net* N, int nx, int ny, int nz, int zs, co
     k_mse<<<lb, 256, 0, s>>>(nvox, N->out, target, 1.f / (float)nvox, N->dA[0], N->lpart);
     count_launch();
     HEC_CHECK(backward(N, g, s));
-    if (update) {
-        N->step++;
-        const float b1 = 0.9f, b2 = 0.999f;
-        const float c1 = 1.f - powf(b1, (float)N->step), c2 = 1.f - powf(b2, (float)N->step);
-        k_adam<<<(NL * PSZ + 255) / 256, 256, 0, s>>>(NL * PSZ, N->P, N->G, N->M, N->V, lr, b1, b2, 1e-8f, c1, c2);
-        count_launch();
-        HEC_CHECK(refresh_weights(N, s));
-    }
     if (loss_out) {
         std::vector<float> h(lb);
         HEC_CUDA(cudaMemcpyAsync(h.data(), N->lpart, sizeof(float) * lb, cudaMemcpyDeviceToHost, s));
@@ -738,5 +730,48 @@ HEC_API hec_status net_train_step(hec_net* N, int nx, int ny, int nz, int zs, co
         *loss_out = (float)(t / (double)nvox);
     }
     HEC_CUDA(cudaGetLastError());
+    return HEC_OK;
+}
+
+// one bias-corrected Adam step on the kept gradients, then the BF16 weight copies
+static hec_status net_adam_impl(hec_net* N, float lr, cudaStream_t s) {
+    if (!N) return set_error(HEC_ERR_INVALID_ARG, "net_adam_step: NULL");
+    N->step++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)N->step), c2 = 1.f - powf(b2, (float)N->step);
+    k_adam<<<(NL * PSZ + 255) / 256, 256, 0, s>>>(NL * PSZ, N->P, N->G, N->M, N->V, lr, b1, b2, 1e-8f, c1, c2);
+    count_launch();
+    HEC_CHECK(refresh_weights(N, s));
+    HEC_CUDA(cudaGetLastError());
+    return HEC_OK;
+}
+
+HEC_API hec_status net_backward(hec_net* N, int nx, int ny, int nz, int zs, const void* x_in, const float* target,
+                                float* loss_out, void* stream) {
+    clear_error();
+    return net_backward_impl(N, nx, ny, nz, zs, x_in, target, loss_out, S(stream), "net_backward");
+}
+
+HEC_API hec_status net_adam_step(hec_net* N, float lr, void* stream) {
+    clear_error();
+    return net_adam_impl(N, lr, S(stream));
+}
+
+HEC_API hec_status net_train_step(hec_net* N, int nx, int ny, int nz, int zs, const void* x_in, const float* target,
+                                  float lr, int update, float* loss_out, void* stream) {
+    clear_error();
+    cudaStream_t s = S(stream);
+    // the loss is read back after the update, as one call of the two steps would
+    HEC_CHECK(net_backward_impl(N, nx, ny, nz, zs, x_in, target, nullptr, s, "net_train_step"));
+    if (update) HEC_CHECK(net_adam_impl(N, lr, s));
+    if (loss_out) {
+        const int lb = 1024;
+        std::vector<float> h(lb);
+        HEC_CUDA(cudaMemcpyAsync(h.data(), N->lpart, sizeof(float) * lb, cudaMemcpyDeviceToHost, s));
+        HEC_CUDA(cudaStreamSynchronize(s));
+        double t = 0.0;
+        for (float v : h) t += v;
+        *loss_out = (float)(t / (double)((long)nx * ny * nz));
+    }
     return HEC_OK;
 }

@@ -182,4 +182,7 @@ inline int default_lanes_per_row(const hec_matrix* T) {
 // (NULL = identity), scatter[r] the row of x receiving it (NULL = identity, -1 = skip).
 hec_status sweep(const sptrsv_plan* p, int nrhs, const double* b, int ldb, const int* gather, double* x,
                  int ldx, const int* scatter, cudaStream_t s);
+// y = alpha A x + beta y for a general-mode FP64 HEC matrix (krylov.cu; no argument checks)
+hec_status spmv_impl(const hec_matrix* A, int K, double alpha, const double* x, int ldx, double beta, double* y,
+                     int ldy, cudaStream_t s);
 }  // namespace hec

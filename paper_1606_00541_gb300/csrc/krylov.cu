@@ -8,11 +8,9 @@
 //
 // Each inner iteration is a fixed sequence of launches with no host round trip:
 //   z_j = M^-1 v_j (ilu_apply), w = A z_j (SpMV),
-//   classical Gram-Schmidt h = V^T w, w -= V h, with ||w||^2 before and after,
-//   a second (re-orthogonalization) pass only when ||w|| dropped below ||w_0|| / sqrt(2)
-//     (the "twice is enough" criterion; the pass is skipped on the device otherwise),
-//   the Hessenberg column, Givens rotations and the convergence test in a one-block kernel,
-//   and w /= h_{j+1,j}.
+//   one persistent cooperative kernel (k_arnoldi_mgs): modified Gram-Schmidt against v_0..v_j
+//     (one pass and one grid-wide reduction per projection), ||w||, the Hessenberg column with
+//     its Givens rotations and the convergence test, and w /= h_{j+1,j}.
 // The host stays one iteration ahead of the device and reads a per-iteration "still active"
 // flag through pinned memory, so the GPU never waits for the host inside a restart cycle.  The
 // host synchronizes once per restart to check the true residual.

@@ -436,32 +436,35 @@ def csr_triangle(rowptr, col, val, uplo, strict=False, stream=None):
     return Csr(out.value)
 
 
-class SgsSmoother:
-    """Symmetric Gauss-Seidel on the level-scheduled sweeps (the smoother use of the triangular
-    solver, Sec. 1): a forward sweep solves (D + L) x' = b - U_s x, a backward sweep
-    (D + U) x'' = b - L_s x'.  Level scheduling only reorders independent rows, so every sweep
-    equals the sequential Gauss-Seidel sweep up to rounding."""
+_sgs_create = _sig("sgs_create", _i, _vp, _vp, _vp, _i, _i, ctypes.POINTER(_vp), _vp)
+_sgs_smooth = _sig("sgs_smooth", _vp, _i, _vp, _i, _vp, _i, _i, _vp)
+_sgs_sync_status = _sig("sgs_sync_status", _vp, _vp)
+_sgs_destroy = _sig("sgs_destroy", _vp)
+
+
+class SgsSmoother(_Handle):
+    """Symmetric Gauss-Seidel on the level-scheduled sweeps (sgs_create / sgs_smooth, include/hec.h):
+    a forward sweep solves (D + L) x' = b - U_s x, a backward sweep (D + U) x'' = b - L_s x'."""
+    _destroy = staticmethod(_sgs_destroy)
 
     def __init__(self, A, vdt="f64", max_nrhs=1, stream=None):
-        DL, Us = csr_triangle(*A, 0, False, stream).tensors(), csr_triangle(*A, 1, True, stream).tensors()
-        DU, Ls = csr_triangle(*A, 1, False, stream).tensors(), csr_triangle(*A, 0, True, stream).tensors()
-        self.lvL = sptrsv_analyze(DL[0], DL[1], 0, stream)
-        self.lvU = sptrsv_analyze(DU[0], DU[1], 1, stream)
-        self.pL = sptrsv_plan_create(hec_from_csr(*DL, levels=self.lvL, vdt=vdt, stream=stream), self.lvL, max_nrhs)
-        self.pU = sptrsv_plan_create(hec_from_csr(*DU, levels=self.lvU, vdt=vdt, stream=stream), self.lvU, max_nrhs)
-        self.Us = hec_from_csr(*Us, vdt="f64", stream=stream)
-        self.Ls = hec_from_csr(*Ls, vdt="f64", stream=stream)
+        n = A[0].numel() - 1
+        out = _vp()
+        _check(_sgs_create(n, _ptr(A[0]), _ptr(A[1]), _ptr(A[2]), DTYPES[vdt], int(max_nrhs), ctypes.byref(out),
+                           _stream(stream)), "sgs_create")
+        super().__init__(out.value)
 
     def smooth(self, x, b, sweeps=1, stream=None):
         """`sweeps` symmetric Gauss-Seidel sweeps from x (device FP64 [n] or [n, k]); returns the
         new iterate (x is not modified)."""
-        r = torch.empty_like(b)
-        for _ in range(sweeps):
-            r.copy_(b)
-            x = sptrsv_lower(self.pL, spmv(self.Us, x, r, alpha=-1.0, beta=1.0, stream=stream), stream=stream)
-            r.copy_(b)
-            x = sptrsv_upper(self.pU, spmv(self.Ls, x, r, alpha=-1.0, beta=1.0, stream=stream), stream=stream)
-        return x
+        y = x.clone()
+        nrhs = _nrhs(b)
+        _check(_sgs_smooth(self.h, nrhs, _ptr(b), _ld(b, nrhs), _ptr(y), _ld(y, nrhs), int(sweeps), _stream(stream)),
+               "sgs_smooth")
+        return y
+
+    def sync_status(self, stream=None):
+        return _sgs_sync_status(self.h, _stream(stream))
 
 
 _lib.net_param_count.restype = _i
@@ -472,6 +475,8 @@ _net_set_params = _sig("net_set_params", _vp, _vp)
 _net_forward = _sig("net_forward", _vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp)
 _net_train_step = _sig("net_train_step", _vp, _i, _i, _i, _i, _vp, _vp, ctypes.c_float, _i,
                        ctypes.POINTER(ctypes.c_float), _vp)
+_net_backward = _sig("net_backward", _vp, _i, _i, _i, _i, _vp, _vp, ctypes.POINTER(ctypes.c_float), _vp)
+_net_adam_step = _sig("net_adam_step", _vp, ctypes.c_float, _vp)
 _stage_create = _sig("stage_create", _vp, _vp, _i, _i, _i, _vp, _d, _d, ctypes.POINTER(_vp))
 _stage_stats = _sig("stage_stats", _vp, ctypes.POINTER(_i), ctypes.POINTER(_i), _i)
 _stage_apply = _sig("stage_apply", _vp, _vp, _vp, _vp)
@@ -523,6 +528,18 @@ class Net(_Handle):
         _check(_net_train_step(self.h, nx, ny, nz, zs or nz, _ptr(x_in), _ptr(target), float(lr), 1 if update else 0,
                                ctypes.byref(loss), _stream(stream)), "net_train_step")
         return loss.value
+
+    def backward(self, x_in, target, dims, zs=None, stream=None):
+        """Forward, loss and backward on one minibatch (net_backward); returns the loss."""
+        nx, ny, nz = dims
+        loss = ctypes.c_float()
+        _check(_net_backward(self.h, nx, ny, nz, zs or nz, _ptr(x_in), _ptr(target), ctypes.byref(loss),
+                             _stream(stream)), "net_backward")
+        return loss.value
+
+    def adam_step(self, lr=1e-3, stream=None):
+        """One Adam step from the gradients of the last backward pass (net_adam_step)."""
+        _check(_net_adam_step(self.h, float(lr), _stream(stream)), "net_adam_step")
 
 
 class Stage(_Handle):
