@@ -150,6 +150,25 @@ def test_gradients_and_adam_match_oracle(hec):
     assert np.max(np.abs(p1 - ref)) <= 1e-6
 
 
+def test_backward_then_adam_equals_train_step(hec):
+    """net_backward followed by net_adam_step is net_train_step: the same loss, gradients and
+    updated parameters, bit for bit, over three steps."""
+    from paper_1606_00541_gb300 import learn
+    rng = np.random.default_rng(9)
+    dims, zs = (32, 8, 4), 2
+    p = learn.init_params(11, last_scale=1.0)
+    a, b = hec.Net(p), hec.Net(p)
+    _, xd = rand_input(rng, dims, zs)
+    T = torch.as_tensor(rng.normal(size=int(np.prod(dims))).astype(np.float32), device="cuda")
+    for _ in range(3):
+        la = a.train_step(xd, T, dims, zs=zs, lr=2e-3)
+        lb = b.backward(xd, T, dims, zs=zs)
+        b.adam_step(lr=2e-3)
+        pa, ga = a.params(grads=True)
+        pb, gb = b.params(grads=True)
+        assert la == lb and np.array_equal(ga, gb) and np.array_equal(pa, pb)
+
+
 def test_training_reduces_loss(hec):
     from paper_1606_00541_gb300 import learn
     rng = np.random.default_rng(4)
@@ -223,47 +242,85 @@ def test_trained_stage_gain(hec):
     assert learned["iterations"] <= plain["iterations"]
 
 
-def test_stage_apply_matches_its_definition(hec):
-    """One stage application against the stage's definition assembled from separate calls: r1 =
-    v - A z1, sigma = RMS(r1), c = sigma Net([r1 / sigma, aux / 2]) (the network run on the packed
-    sample of net_make_sample), alpha = <r1, Ac> / <Ac, Ac>, z = z1 + alpha c.  The stage reads r1
-    and aux directly in its first layer and writes c from its last, so this checks the fused
-    input and output paths; an x extent of 37 leaves a ragged 32-wide tile."""
-    import ctypes
-    from paper_1606_00541_gb300 import learn
+def layers_to_params(layers):
+    """Oracle layers [(W[dz,dy,dx,ci,co], b)] -> the flat FP32 parameter array of the C ABI (weight
+    (tap, ci, co) at (tap*16 + ci)*16 + co, tap = (dz*3 + dy)*3 + dx, then the 16 biases)."""
+    p = np.zeros(4 * LAYER, dtype=np.float32)
+    for li, (W, b) in enumerate(layers):
+        ci, co = W.shape[3], W.shape[4]
+        Wf = np.zeros((27, C, C), dtype=np.float32)
+        Wf[:, :ci, :co] = W.reshape(27, ci, co)
+        p[li * LAYER:li * LAYER + 27 * C * C] = Wf.reshape(-1)
+        p[li * LAYER + 27 * C * C:li * LAYER + 27 * C * C + co] = b
+    return p
+
+
+def random_layers(seed, scale=0.3):
+    """The identity net of the stage oracle with every weight and bias perturbed by seeded noise
+    (He-normal times `scale`, as FP32 values): all 27 taps and 16 channels of every layer carry
+    random values, while the output stays close enough to the first input channel that the step
+    length alpha is positive."""
+    from oracle import stage_ref
+    rng = np.random.default_rng(seed)
+    out = []
+    for W0, b0 in stage_ref.identity_layers():
+        ci = W0.shape[3]
+        W = W0 + scale * rng.normal(0.0, np.sqrt(2.0 / (27 * ci)), size=W0.shape)
+        b = b0 + 0.05 * scale * rng.normal(size=b0.shape)
+        out.append((W.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)))
+    return out
+
+
+@pytest.mark.parametrize("net_kind", ["identity", "random"])
+def test_stage_apply_matches_oracle(hec, net_kind):
+    """One stage application (stage_apply through the C ABI) against oracle/stage_ref.stage_step on
+    the same inputs: A, v, z1 = the oracle's FP64 ILU(0) apply, the same FP32 weights and the same
+    aux field; the oracle evaluates the network BF16-faithfully (weights, inputs and hidden
+    activations rounded as the kernels store them, FP64 arithmetic).  An x extent of 37 leaves a
+    ragged 32-wide tile.
+    - identity net (every weight +-1, output = its first input channel): the network path is exact
+      in BF16, so c, alpha and z agree to the FP32 partial sums alpha is taken from (1e-5);
+    - perturbed net (identity plus seeded noise on every weight and bias): c differs by
+      accumulation order (FP32 against FP64) and the BF16
+      rounding flips it causes in the hidden layers, 8 significant bits at worst per value:
+      ||c - c_ref|| <= 2^-6 ||c_ref||, alpha within 2^-6, z within 2^-5 ||alpha c||.
+    Both with rho = 1e12 (always accepted) and rho = 1e-12 (always the fallback, z = z1 bit for
+    bit), and with rho between, the oracle's decision."""
+    from oracle import ilu0, ilu_apply, stage_ref
     dims = (37, 20, 18)
     n = int(np.prod(dims))
     lnk = np.random.default_rng(np.random.PCG64(31)).normal(0.0, 2.0, size=n)
     nx, ny, nz = dims
     A = synth.fv7_lognormal_box(nx, ny, nz, perm=np.exp(lnk))
+    L, U = ilu0(A)
+    v = synth.uniform_vector(n, 8)
+    z1 = ilu_apply(L, U, v)
+    layers = stage_ref.identity_layers() if net_kind == "identity" else random_layers(41)
+    net = hec.Net(layers_to_params(layers))
     Ad = [torch.as_tensor(a, device="cuda") for a in A]
-    Lh, Uh = hec.ilu_factor(*Ad, k=0)
-    s = hec.IluSolver(Lh.tensors(), Uh.tensors(), A=Ad, vdt="f32")
-    net = hec.Net(learn.init_params(4, last_scale=1.0))
+    HA = hec.hec_from_csr(*Ad)
     aux = torch.as_tensor(lnk, device="cuda")
-    v = torch.as_tensor(synth.uniform_vector(n, 8), device="cuda")
-    z1 = s.apply(v)
-    stage = hec.Stage(net, s.A, dims, aux, rho=1e12)
-    z = stage.apply(v, z1)
-    # the definition, one call at a time
-    r1 = hec.spmv(s.A, z1, v.clone(), alpha=-1.0, beta=1.0)
-    x = torch.empty(n, C, dtype=torch.bfloat16, device="cuda")
-    sig = torch.empty(1, dtype=torch.float64, device="cuda")
-    st = torch.cuda.current_stream().cuda_stream
-    hec._check(hec._lib.net_make_sample(ctypes.c_int(n), ctypes.c_void_p(r1.data_ptr()), None,
-                                        ctypes.c_void_p(aux.data_ptr()), ctypes.c_double(0.5),
-                                        ctypes.c_void_p(x.data_ptr()), None, ctypes.c_void_p(sig.data_ptr()),
-                                        ctypes.c_void_p(st)), "net_make_sample")
-    out = net.forward(x, dims)
-    c = sig * out.double()
-    Ac = hec.spmv(s.A, c)
-    alpha = float(torch.dot(r1, Ac) / torch.dot(Ac, Ac))
-    assert alpha > 0.0
-    zr = z1 + alpha * c
-    # the stage takes alpha's inner products with FP32 partial sums: alpha within ~1e-6
-    tol = 1e-5 * float(torch.max(torch.abs(alpha * c))) + 1e-12 * float(torch.max(torch.abs(zr)))
-    assert float(torch.max(torch.abs(z - zr))) <= tol
+    vd, z1d = torch.as_tensor(v, device="cuda"), torch.as_tensor(z1, device="cuda")
+    ref = stage_ref.stage_step(A, v, z1, layers, lnk, dims, rho=1e12, aux_scale=0.5, bf16=True)
+    assert ref["alpha"] > 0.0 and ref["accepted"]
+    stage = hec.Stage(net, HA, dims, aux, aux_scale=0.5, rho=1e12)
+    z = stage.apply(vd, z1d).cpu().numpy()
     assert stage.stats()["accepted"] == 1
+    ac = ref["alpha"] * ref["c"]
+    if net_kind == "identity":
+        assert np.max(np.abs(z - ref["z"])) <= 1e-5 * np.max(np.abs(ac)) + 1e-14 * np.max(np.abs(ref["z"]))
+    else:
+        c_gpu = (z - z1)  # = alpha_gpu c_gpu
+        assert np.linalg.norm(c_gpu - ac) <= 2.0 ** -5 * np.linalg.norm(ac)
+        assert abs(np.dot(c_gpu, ac) / np.dot(ac, ac) - 1.0) <= 2.0 ** -6
+    print(net_kind, "alpha %.6f reduction %.4f, |z - z_ref| / |alpha c| = %.3e"
+          % (ref["alpha"], ref["reduction"], np.linalg.norm(z - ref["z"]) / np.linalg.norm(ac)))
     # the fallback returns z1 itself
-    never = hec.Stage(net, s.A, dims, aux, rho=1e-12)
-    assert torch.equal(never.apply(v, z1), z1)
+    never = hec.Stage(net, HA, dims, aux, aux_scale=0.5, rho=1e-12)
+    assert torch.equal(never.apply(vd, z1d), z1d)
+    assert not stage_ref.stage_step(A, v, z1, layers, lnk, dims, rho=1e-12, bf16=True)["accepted"]
+    # a threshold on either side of the oracle's reduction gives the oracle's decision
+    for rho in (ref["reduction"] * 1.05, ref["reduction"] * 0.95):
+        st = hec.Stage(net, HA, dims, aux, aux_scale=0.5, rho=rho)
+        st.apply(vd, z1d)
+        assert bool(st.stats()["accepted"]) == (ref["reduction"] < rho), rho
