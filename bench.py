@@ -248,11 +248,16 @@ def main():
                     help="at most this many timed oracle steps (each a whole solve) in the reference arm")
     ap.add_argument("--sweep", default="part", choices=["part", "global"],
                     help="single-RHS sweep schedule of the timed step: x-pencil partitioned (default) or global")
+    ap.add_argument("--apply-only", choices=["ilu0_16rhs", "ras64_16rhs"], default=None,
+                    help="only time the 16-right-hand-side L+U apply of this preconditioner (a short run, e.g. "
+                         "to profile the multi-right-hand-side sweep)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.apply_only:
+        return run_apply_only(args)
 
     import torch
     import torch.distributed as dist
@@ -381,6 +386,18 @@ def main():
             % (os.path.relpath(SWEEP_PROFILES[args.sweep], ROOT), sweep_source_digest()) if tr is not None
             else "none: the sweep sources changed since the committed capture")
     if rank == 0:
+        # where one solve's device time goes, by kernel class (an untimed solve with every launch
+        # bracketed by events)
+        torch.cuda.synchronize()
+        hec.profile_enable(True)
+        hec.profile_read(reset=True)
+        step()
+        torch.cuda.synchronize()
+        br = hec.profile_breakdown()
+        hec.profile_read(reset=True)
+        hec.profile_enable(False)
+        line["breakdown_ms"] = {k: round(v[0], 3) for k, v in br.items()}
+    if rank == 0:
         # the metric's comparison, short enough to stay in view: FP64 against mixed-precision
         # factors, time to 1e-8 with the bench's schedule
         pt = precision_times(hec, torch, Ad, L, U, bd, sched)
@@ -393,6 +410,7 @@ def main():
                 if "latency_floor" in roofline:
                     head["latency_floor_us"] = roofline["latency_floor"]["floor_us"]
                     head["sweep_us"] = roofline["avg_sweep_us"]
+                head["breakdown_ms"] = line.get("breakdown_ms")
         line = head
     if rank == 0 and not args.no_variants:
         line["variants"] = variants(hec, torch, Ad, L, U, bd, HA0, n, nnzL, nnzU, hbm, Schedule("part", m, devn, torch))
@@ -711,6 +729,45 @@ def long_row_variant(hec, torch, hbm, device, m=100, ilut=None):
         res["nrhs16"] = {"lu_us": t16 * 1e6, "lu_gbs": B16 / t16 / 1e9, "frac_hbm": B16 / t16 / 1e9 / hbm}
         out[vdt] = res
     return out
+
+
+def run_apply_only(args):
+    """The 16-right-hand-side L+U apply of one preconditioner (GPU ILU(0) of the whole matrix, or
+    RAS with 64 box subdomains), FP32 factor values, autotuned launch shape: W untimed and K timed
+    applies; prints one JSON line with the apply time and its algorithmic GB/s."""
+    import torch
+    from paper_1606_00541_gb300 import hec, synth
+    m = args.size
+    n = m ** 3
+    A, _ = make_problem(m)
+    Ad = [torch.as_tensor(a, device="cuda") for a in A]
+    B = torch.as_tensor(synth.uniform_vector(n, 500, nrhs=16), device="cuda")
+    if args.apply_only == "ras64_16rhs":
+        part, ns = synth.box_partition(m, ras_cuts(m))
+        s = hec.RasSolver(Ad, torch.as_tensor(part, device="cuda"), ns, vdt="f32", max_nrhs=16)
+        nnzl, nnzu = int(s.L[1].numel()), int(s.U[1].numel())
+    else:
+        Lh, Uh = hec.ilu_factor(*Ad, k=0)
+        L, U = Lh.tensors(), Uh.tensors()
+        s = hec.IluSolver(L, U, vdt="f32", max_nrhs=16)
+        nnzl, nnzu = int(L[1].numel()), int(U[1].numel())
+    shapes = s.autotune(16)
+    for _ in range(args.warmup):
+        s.apply(B)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        s.apply(B)
+    e1.record()
+    torch.cuda.synchronize()
+    ta = e0.elapsed_time(e1) / 1000.0 / args.steps
+    nl = s.HL.info().n
+    Bytes = sweep_bytes(nnzl, nl, 16, 4) + sweep_bytes(nnzu, nl, 16, 4)
+    hbm, src = peaks()
+    print(json.dumps({"apply": args.apply_only, "rows": nl, "levels_L": s.lvL.nlev, "levels_U": s.lvU.nlev,
+                      "lu_apply_us": ta * 1e6, "bytes": Bytes, "lu_gbs": Bytes / ta / 1e9,
+                      "frac_hbm": Bytes / ta / 1e9 / hbm, "launch_shape": shapes}), flush=True)
 
 
 def batched_variants(hec, torch, Ad, L, U, n, hbm):

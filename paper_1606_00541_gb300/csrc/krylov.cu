@@ -30,6 +30,8 @@ namespace hec {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kMgsThreads = 1024;  // the persistent Arnoldi kernel: few, large blocks, so that the
+                                   // per-projection sum over the blocks' partials stays short
 constexpr int kDotGroup = 8;  // dot products per block row of the multi-dot
 
 // y = alpha A x + beta y for K right-hand sides (x, y row-major with leading dimensions ldx,
@@ -236,12 +238,12 @@ __device__ bool arnoldi_column(const ArnoldiState& st, int K, int j, int m, doub
 // w /= h_{j+1,j}.  FP64 throughout.  Reductions are deterministic: each block writes its partial
 // sum, and every block adds all partials in the same fixed order (double-buffered by step).
 template <int KP>
-__global__ void __launch_bounds__(kThreads) k_arnoldi_mgs(int n, int K, int j, int m, double rtol,
+__global__ void __launch_bounds__(kMgsThreads) k_arnoldi_mgs(int n, int K, int j, int m, double rtol,
                                                           const double* __restrict__ V, long vstride, double* w,
                                                           double* partial, ArnoldiState st) {
     cg::grid_group grid = cg::this_grid();
-    constexpr int RPB = kThreads / KP;
-    __shared__ double red[kThreads / 32][KP];
+    constexpr int RPB = kMgsThreads / KP;
+    __shared__ double red[kMgsThreads / 32][KP];
     __shared__ double hsh[KP];
     __shared__ int any;
     const int q = threadIdx.x % KP;
@@ -258,18 +260,18 @@ __global__ void __launch_bounds__(kThreads) k_arnoldi_mgs(int n, int K, int j, i
         __syncthreads();
         if (threadIdx.x < KP) {
             double s = 0.0;
-            for (int wi = 0; wi < kThreads / 32; ++wi) s += red[wi][threadIdx.x];
+            for (int wi = 0; wi < kMgsThreads / 32; ++wi) s += red[wi][threadIdx.x];
             partial[((long)buf * nb + blockIdx.x) * KP + threadIdx.x] = s;
         }
         grid.sync();
-        if (warp == 0) {
-            for (int qq = 0; qq < KP; ++qq) {
-                double s = 0.0;
-                for (int b = lane; b < nb; b += 32) s += partial[((long)buf * nb + b) * KP + qq];
+        // every block adds the blocks' partial sums in the same fixed order, warp qq for right-hand
+        // side qq
+        if (warp < KP) {
+            double s = 0.0;
+            for (int b = lane; b < nb; b += 32) s += partial[((long)buf * nb + b) * KP + warp];
 #pragma unroll
-                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == 0) hsh[qq] = s;
-            }
+            for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) hsh[warp] = s;
         }
         __syncthreads();
     };
@@ -378,7 +380,7 @@ struct Mgs {
     double* partial = nullptr;
     int cap_blocks = 0;
     hec_status init() {
-        cap_blocks = num_sms() * (2048 / kThreads);
+        cap_blocks = num_sms() * (2048 / kMgsThreads);
         return dalloc(&partial, (size_t)2 * cap_blocks * 16);
     }
     ~Mgs() { cudaFree(partial); }
@@ -387,14 +389,14 @@ struct Mgs {
                       ArnoldiState& st, cudaStream_t s) {
         const void* k = (const void*)k_arnoldi_mgs<KP>;
         static int per_sm = -1;  // per template instance
-        if (per_sm < 0) per_sm = max_coop_blocks(k, kThreads, 0);
+        if (per_sm < 0) per_sm = max_coop_blocks(k, kMgsThreads, 0);
         if (per_sm <= 0) return set_error(HEC_ERR_CUDA, "Arnoldi kernel cannot be resident");
-        const long want = ((long)n * KP + kThreads - 1) / kThreads;
+        const long want = ((long)n * KP + kMgsThreads - 1) / kMgsThreads;
         int blocks = (int)std::max(1L, std::min<long>(std::min(per_sm * num_sms(), cap_blocks), want));
         double* part = partial;
         void* args[] = {&n, &K, &j, &m, &rtol, (void*)&V, &vstride, &w, &part, &st};
         ProfScope ps_(s, PROF_GS);
-        HEC_CUDA(cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(kThreads), args, 0, s));
+        HEC_CUDA(cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(kMgsThreads), args, 0, s));
         count_launch();
         return HEC_OK;
     }
