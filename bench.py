@@ -525,7 +525,13 @@ def learned_variant(hec, torch, m, seed=0, crop=32, crops=125, epochs=8, log=Non
     Lh, Uh = hec.ilu_factor(*Ad, k=0)
     s = hec.IluSolver(Lh.tensors(), Uh.tensors(), A=Ad, vdt="f32")
     b = hec.spmv(s.A, torch.as_tensor(synth.uniform_vector(m ** 3, seed + 1), device="cuda"))
-    schedule = pick_schedule(hec, torch, s, m, b)  # the faster single-RHS schedule, for both forms
+    # the single-RHS schedule for both forms: the library's autotuner keeps the x-pencil partition
+    # or the global sweep, whichever is faster on these factors
+    sched = Schedule("part", m, b.device, torch)
+    sched.apply(s)
+    tuned = s.autotune(1)
+    schedule = ("x-pencil partitioned, %d parts" % sched.nparts if all(t["partitioned"] for t in tuned)
+                else "global") + " (sptrsv_autotune: %s)" % (list(tuned),)
     stage = hec.Stage(net, s.A, (m, m, m), torch.as_tensor(lnk, device="cuda"), rho=0.99)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     res = {"train": tinfo, "sweep_schedule": schedule}
@@ -572,30 +578,6 @@ class Schedule:
         if self.kind == "part":
             return "x-pencil partitioned: %d parts, %d threads per part" % (self.nparts, PART_THREADS)
         return "global level-ordered"
-
-
-def pick_schedule(hec, torch, s, m, b, reps=5):
-    """Times the ILU apply with the global sweep and with the x-pencil partition and keeps the
-    faster one on the solver; returns a description with both times."""
-    def t_apply():
-        s.apply(b)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            s.apply(b)
-        torch.cuda.synchronize()
-        return (time.perf_counter() - t0) / reps
-    tg = t_apply()
-    part_d, nparts = sweep_partition(torch, m, b.device)
-    try:
-        s.partition(part_d, nparts, threads=PART_THREADS)
-    except hec.HecError as e:
-        return "global (partition refused: %s)" % e
-    tp = t_apply()
-    if tp < tg:
-        return "x-pencil partitioned, %d parts (L+U %.0f us; global %.0f us)" % (nparts, tp * 1e6, tg * 1e6)
-    s.partition(None, 0)
-    return "global (L+U %.0f us; partitioned %.0f us)" % (tg * 1e6, tp * 1e6)
 
 
 def chain_csr(n):
@@ -647,18 +629,12 @@ def level_floor(hec, torch, device, levels, crossings, threads, vdt="f32", n=409
             "method": "bidiagonal chain of %d rows, one part / two alternating parts, %d threads" % (n, threads)}
 
 
-def sweep_partition(torch, m, device):
-    """x-pencils for the partitioned single-RHS sweep: the y-z plane cut into 12 x 12 boxes (144
-    parts, one resident 1024-thread block each), so a dependency chain crosses a part boundary at
-    most 22 times and every other step stays in one SM's shared memory.  Grids above 160^3 take
-    8 x 19 pencils (152 parts) so that a part's FP32 solution still fits in shared memory."""
-    from paper_1606_00541_gb300 import synth
-    part, nparts = synth.grid_boxes(m, sweep_grid(m))
-    return torch.as_tensor(part, device=device), nparts
-
-
 def sweep_grid(m):
-    """Boxes per axis of the x-pencil partition used on an m^3 grid."""
+    """Boxes per axis of the x-pencil partition used on an m^3 grid: the y-z plane cut into 12 x 12
+    boxes (144 parts, one resident 1024-thread block each), so a dependency chain crosses a part
+    boundary at most 22 times and every other step stays in one SM's shared memory.  Grids above
+    160^3 take 8 x 19 pencils (152 parts) so that a part's FP32 solution still fits in shared
+    memory."""
     return (1, 12, 12) if m <= 160 else (1, 8, 19)
 
 
@@ -671,8 +647,8 @@ def ras_cuts(m):
 def long_row_variant(hec, torch, hbm, device, m=100, ilut=None):
     """Long rows: the 27-point jittered stencil on 100^3 (a_ii = 1.05 sum |a_ij|, +-30 % jitter)
     with its GPU ILU(0) (13 strictly lower entries per interior row) or GPU ILUT(p, tol);
-    single-RHS L+U apply with one lane per row against the lanes per row the plan picks from the
-    row length, 16-RHS L+U, and FGMRES(30) to 1e-8 with FP32 and FP64 factor values."""
+    single-RHS L+U apply with one lane per row against the autotuned plans (launch shape and lanes
+    per row of each factor), 16-RHS L+U, and FGMRES(30) to 1e-8 with FP32 and FP64 factor values."""
     from paper_1606_00541_gb300 import synth
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     A = [torch.as_tensor(a, device=device) for a in synth.stencil27_jitter(m, seed=0)]
@@ -691,6 +667,7 @@ def long_row_variant(hec, torch, hbm, device, m=100, ilut=None):
         res = {}
         for lpr in (1, 0):
             s = hec.IluSolver(L, U, A=A, vdt=vdt, lanes_per_row=lpr)
+            tuned = s.autotune(1) if lpr == 0 else None  # launch shape and lanes per row by the autotuner
             for _ in range(3):
                 s.apply(b)
             torch.cuda.synchronize()
@@ -701,7 +678,8 @@ def long_row_variant(hec, torch, hbm, device, m=100, ilut=None):
             torch.cuda.synchronize()
             ta = e0.elapsed_time(e1) / 1000.0 / 10
             B = sweep_bytes(nnzL, n, 1, sv) + sweep_bytes(nnzU, n, 1, sv)
-            key = "one_lane" if lpr == 1 else "lanes_%d" % hec.sptrsv_autotune(s.pL, 1)["lanes_per_row"]
+            key = "one_lane" if lpr == 1 else "autotuned_lanes_%d_%d" % (tuned[0]["lanes_per_row"],
+                                                                           tuned[1]["lanes_per_row"])
             res[key] = {"lu_us": ta * 1e6, "lu_gbs": B / ta / 1e9, "frac_hbm": B / ta / 1e9 / hbm}
             if lpr == 0:
                 s.solve(b, restart=RESTART, rtol=RTOL, max_iters=5000)

@@ -176,6 +176,10 @@ typedef struct {
                                to 6 / 12 / wider).  Several lanes poll all of a long row's
                                dependencies in one wait and add their partial sums with an xor
                                butterfly (a different summation order from one lane). */
+    int partitioned;        /* output of sptrsv_autotune: 1 when single-right-hand-side sweeps of
+                               the plan take its partition (sptrsv_plan_partition), 0 when the
+                               global schedule was faster or there is no partition; ignored as
+                               an input */
 } hec_tune;
 
 /* A solve plan for one triangular factor: its HEC form and level analysis (both borrowed; they
@@ -214,13 +218,17 @@ hec_status sptrsv_plan_partition(sptrsv_plan* p, const int* part, int nparts, in
                                  void* stream);
 int sptrsv_partition_capacity(const sptrsv_plan* p, int threads);
 
-/* Autotuner: times the plan's own sweep (on a zero right-hand side, nrhs columns) for the
- * candidate launch shapes block_threads in {128, 256} x blocks_per_sm in {2, 4, 8, 16} (those that
- * fit 2048 threads per SM) and stores the fastest in the plan; `out` (host, may be NULL) receives
- * it.  Results are cached per (rows, slab width, tail entries, levels, value type, nrhs rounded up
- * to a power of two) for the life of the process.  Synchronizes `stream`.  The point-to-point
- * sweep has no per-level barriers, so the paper's level-merging threshold has no counterpart;
- * residency is the parameter that matters. */
+/* Autotuner: times the plan's own sweep (on a zero right-hand side, nrhs columns) and keeps the
+ * fastest of the candidates in the plan; `out` (host, may be NULL) receives the choice.
+ * Candidates: launch shapes block_threads in {128, 256} x blocks_per_sm in {2, 4, 8, 16} (those
+ * that fit 2048 threads per SM); for nrhs = 1 also lanes per row in {1, 2, 4, 8} (one thread per
+ * row against several lanes sharing a long row), and, when the plan has a partition
+ * (sptrsv_plan_partition), the partitioned schedule against the best global one (a plan whose
+ * global schedule wins keeps its partition unused; partitioning it again re-enables it).
+ * Results are cached per (rows, slab width, tail entries, levels, value type, nrhs rounded up to
+ * a power of two, partition given) for the life of the process.  Synchronizes `stream`.  The
+ * point-to-point sweep has no per-level barriers, so the paper's level-merging threshold has no
+ * counterpart. */
 hec_status sptrsv_autotune(sptrsv_plan* p, int nrhs, hec_tune* out, void* stream);
 
 /* Reads and clears the device status word of a plan (synchronizes `stream`).  Returns HEC_OK,

@@ -127,6 +127,7 @@ struct sptrsv_plan {
     int nchunks[5] = {};
     void* dinv = nullptr;      // reciprocal diagonal in the work type (NULL: the kernel divides)
     int lpr1 = 1;              // lanes per row of single-right-hand-side sweeps (1, 2, 4 or 8)
+    int use_part = 1;          // single-right-hand-side sweeps take the partition when there is one
 };
 
 struct ilu_precond {

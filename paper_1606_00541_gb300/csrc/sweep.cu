@@ -1058,19 +1058,18 @@ __global__ void k_chunk_table(int nlev, const int* __restrict__ level_ptr, const
     tbl[c] = make_int2(row0, min(rpw, level_ptr[lo + 1] - row0));
 }
 
-hec_status build_chunks(sptrsv_plan* p) {
+// the chunk tables of the lane layouts in `needed` (bit i: 32 >> i rows per warp step) that the
+// plan does not have yet
+hec_status build_chunks(sptrsv_plan* p, unsigned needed) {
     const hec_levels* lv = p->lv;
     const int nlev = lv->nlev;
     int* cptr = nullptr;
     HEC_CHECK(dalloc(&cptr, (size_t)nlev + 1));
     hec_status st = HEC_OK;
     cudaStream_t s = 0;
-    unsigned needed = 0;  // only the lane layouts this plan can be called with
-    for (int k = 1; k <= p->max_nrhs; ++k) needed |= 1u << log2i(sweep_lpr(k, p->T->vdt));
-    needed |= 1u << log2i(p->lpr1);
     for (int i = 0; i < 5 && st == HEC_OK; ++i) {
         const int rpw = 32 >> i;
-        if (!(needed & (1u << i))) continue;
+        if (!(needed & (1u << i)) || p->chunks[i]) continue;
         if (nlev > 0) {
             k_chunk_counts<<<(nlev + 255) / 256, 256, 0, s>>>(nlev, lv->level_ptr, rpw, cptr);
             count_launch();
@@ -1139,7 +1138,7 @@ hec_status sweep(const sptrsv_plan* pl, int nrhs, const double* b, int ldb, cons
                  const int* scatter, cudaStream_t s) {
     const hec_matrix* T = pl->T;
     if (T->n == 0) return HEC_OK;
-    if (pl->part && nrhs == 1) {
+    if (pl->part && pl->use_part && nrhs == 1) {
         const hec_part_data* P = pl->part;
         PartParams pp;
         pp.n = T->n;
@@ -1488,7 +1487,9 @@ HEC_API hec_status sptrsv_plan_create(const hec_matrix* tri, const hec_levels* l
     hec_status st = dmalloc(&p->xp, work_size(tri->vdt) * (size_t)tri->n * sweep_kp(max_nrhs) + 16);
     if (st == HEC_OK) st = dalloc(&p->status, 1);
     if (st == HEC_OK && cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) st = cuda_error(cudaGetLastError(), "memset");
-    if (st == HEC_OK) st = build_chunks(p);
+    unsigned needed = 1u << log2i(p->lpr1);  // only the lane layouts this plan can be called with
+    for (int k = 1; k <= max_nrhs; ++k) needed |= 1u << log2i(sweep_lpr(k, tri->vdt));
+    if (st == HEC_OK) st = build_chunks(p, needed);
     if (st == HEC_OK) st = build_dinv(p);
     if (st != HEC_OK) { free_plan(p); return st; }
     *out = p;
@@ -1532,6 +1533,7 @@ HEC_API hec_status sptrsv_plan_partition(sptrsv_plan* p, const int* part, int np
     p->part = tmp.part;
     tmp.part = nullptr;
     p->part->threads = threads;
+    p->use_part = 1;
     return HEC_OK;
 }
 
@@ -1565,27 +1567,52 @@ HEC_API hec_status sptrsv_upper(const sptrsv_plan* p, int nrhs, const double* b,
 }
 
 // ---- autotuner ------------------------------------------------------------------------------
-// Residency is the one free parameter of the point-to-point sweep: too few resident warps and a
-// level's rows are not all in flight; too many and far-ahead warps only add polling traffic.  The
-// tuner times the plan's own sweep for a few (block size, blocks per SM) candidates and keeps
-// the fastest; results are cached per matrix signature (rows, slab width, tail entries, levels,
-// value type, right-hand sides) so identical factors are tuned once per process.
+// The free parameters of the point-to-point sweep, searched on the plan's own factor:
+//  - residency (block size x blocks per SM): too few resident warps and a level's rows are not
+//    all in flight; too many and far-ahead warps only add polling traffic;
+//  - for one right-hand side, lanes per row (1, 2, 4 or 8): one lane per row (thread per row)
+//    against several lanes sharing a row's dependencies and a shuffle reduction (the
+//    thread-versus-warp choice by row length);
+//  - for one right-hand side on a plan given a partition, the partitioned schedule against the
+//    best global one.
+// The point-to-point sweep has no per-level barriers, so the paper's level-merging threshold has
+// no counterpart.  Results are cached per matrix signature (rows, slab width, tail entries,
+// levels, value type, right-hand sides, whether a partition was given) so identical factors are
+// tuned once per process.
 namespace {
 struct TuneKey {
-    int n, w, nlev, vdt, kp;
+    int n, w, nlev, vdt, kp, parted;
     long long tail;
     bool operator==(const TuneKey& o) const {
-        return n == o.n && w == o.w && nlev == o.nlev && vdt == o.vdt && kp == o.kp && tail == o.tail;
+        return n == o.n && w == o.w && nlev == o.nlev && vdt == o.vdt && kp == o.kp && parted == o.parted &&
+               tail == o.tail;
     }
 };
 struct TuneKeyHash {
     size_t operator()(const TuneKey& k) const {
         return std::hash<long long>()(((long long)k.n * 1315423911LL) ^ (k.tail * 2654435761LL) ^ (k.nlev * 97) ^
-                                      (k.w * 31 + k.vdt * 7 + k.kp));
+                                      (k.w * 31 + k.vdt * 7 + k.kp * 3 + k.parted));
     }
 };
+struct TuneChoice {
+    int threads, blocks, lpr1, use_part;
+};
 std::mutex g_tune_mu;
-std::unordered_map<TuneKey, std::pair<int, int>, TuneKeyHash> g_tune_cache;
+std::unordered_map<TuneKey, TuneChoice, TuneKeyHash> g_tune_cache;
+
+void apply_choice(sptrsv_plan* p, const TuneChoice& c, hec_tune* out) {
+    p->threads = c.threads;
+    p->blocks = c.blocks;
+    p->lpr1 = c.lpr1;
+    p->use_part = c.use_part;
+    if (out) {
+        *out = hec_tune{};
+        out->block_threads = c.threads;
+        out->blocks_per_sm = c.blocks;
+        out->lanes_per_row = c.lpr1;
+        out->partitioned = (p->part && c.use_part) ? 1 : 0;
+    }
+}
 }  // namespace
 
 HEC_API hec_status sptrsv_autotune(sptrsv_plan* p, int nrhs, hec_tune* out, void* stream) {
@@ -1595,14 +1622,14 @@ HEC_API hec_status sptrsv_autotune(sptrsv_plan* p, int nrhs, hec_tune* out, void
     const hec_matrix* T = p->T;
     int kp = 1;
     while (kp < nrhs) kp <<= 1;
-    TuneKey key{T->n, T->w, p->lv->nlev, (int)T->vdt, kp, T->tail_nnz};
+    const int parted = (nrhs == 1 && p->part) ? 1 : 0;
+    TuneKey key{T->n, T->w, p->lv->nlev, (int)T->vdt, kp, parted, T->tail_nnz};
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            p->threads = it->second.first;
-            p->blocks = it->second.second;
-            if (out) { *out = hec_tune{}; out->block_threads = p->threads; out->blocks_per_sm = p->blocks; out->lanes_per_row = p->lpr1; }
+            if (nrhs == 1) HEC_CHECK(build_chunks(p, 1u << log2i(it->second.lpr1)));
+            apply_choice(p, it->second, out);
             return HEC_OK;
         }
     }
@@ -1616,39 +1643,55 @@ HEC_API hec_status sptrsv_autotune(sptrsv_plan* p, int nrhs, hec_tune* out, void
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int saved_t = p->threads, saved_b = p->blocks;
+    const TuneChoice saved{p->threads, p->blocks, p->lpr1, p->use_part};
+    // one warm-up and three timed sweeps of the plan as it is set
+    auto time_it = [&](float* ms) -> hec_status {
+        hec_status r = sweep(p, nrhs, b, nrhs, p->lv->iperm, x, nrhs, p->lv->iperm, s);
+        if (r) return r;
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < 3 && r == HEC_OK; ++k) r = sweep(p, nrhs, b, nrhs, p->lv->iperm, x, nrhs, p->lv->iperm, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        *ms = 0.f;
+        cudaEventElapsedTime(ms, e0, e1);
+        return r;
+    };
     float best = 1e30f;
-    int bt = saved_t, bb = saved_b;
+    TuneChoice bc = saved;
     const int cand_t[2] = {128, 256};
     const int cand_b[4] = {2, 4, 8, 16};
-    for (int ti = 0; ti < 2 && st == HEC_OK; ++ti) {
-        for (int bi = 0; bi < 4 && st == HEC_OK; ++bi) {
-            if (cand_t[ti] * cand_b[bi] > 2048) continue;
-            p->threads = cand_t[ti];
-            p->blocks = cand_b[bi];
-            st = sweep(p, nrhs, b, nrhs, p->lv->iperm, x, nrhs, p->lv->iperm, s);  // warm
-            if (st) break;
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < 3 && st == HEC_OK; ++r) st = sweep(p, nrhs, b, nrhs, p->lv->iperm, x, nrhs, p->lv->iperm, s);
-            cudaEventRecord(e1, s);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (st == HEC_OK && ms < best) { best = ms; bt = cand_t[ti]; bb = cand_b[bi]; }
+    const int cand_l[4] = {1, 2, 4, 8};
+    for (int li = 0; li < (nrhs == 1 ? 4 : 1) && st == HEC_OK; ++li) {
+        const int lpr = nrhs == 1 ? cand_l[li] : saved.lpr1;
+        if (nrhs == 1 && (st = build_chunks(p, 1u << log2i(lpr)))) break;
+        for (int ti = 0; ti < 2 && st == HEC_OK; ++ti) {
+            for (int bi = 0; bi < 4 && st == HEC_OK; ++bi) {
+                if (cand_t[ti] * cand_b[bi] > 2048) continue;
+                const TuneChoice c{cand_t[ti], cand_b[bi], lpr, 0};
+                apply_choice(p, c, nullptr);
+                float ms = 0.f;
+                st = time_it(&ms);
+                if (st == HEC_OK && ms < best) { best = ms; bc = c; }
+            }
         }
+    }
+    if (st == HEC_OK && parted) {  // the partitioned schedule (its launch shape is the partition's)
+        const TuneChoice c{bc.threads, bc.blocks, bc.lpr1, 1};
+        apply_choice(p, c, nullptr);
+        float ms = 0.f;
+        st = time_it(&ms);
+        if (st == HEC_OK && ms < best) { best = ms; bc = c; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(b);
     cudaFree(x);
-    if (st) { p->threads = saved_t; p->blocks = saved_b; return st; }
-    p->threads = bt;
-    p->blocks = bb;
+    if (st) { apply_choice(p, saved, nullptr); return st; }
+    apply_choice(p, bc, out);
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
-        g_tune_cache[key] = {bt, bb};
+        g_tune_cache[key] = bc;
     }
-    if (out) { *out = hec_tune{}; out->block_threads = bt; out->blocks_per_sm = bb; out->lanes_per_row = p->lpr1; }
     return hec_sync_status(p, stream);
 }
 

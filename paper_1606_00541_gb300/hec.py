@@ -44,7 +44,7 @@ class HecMatrixInfo(ctypes.Structure):
 
 class HecTune(ctypes.Structure):
     _fields_ = [("block_threads", _i), ("blocks_per_sm", _i), ("wait_cycles", _ll), ("debug_unpublished_row", _i),
-                ("backoff_ns", _i), ("lanes_per_row", _i)]
+                ("backoff_ns", _i), ("lanes_per_row", _i), ("partitioned", _i)]
 
 
 class HecFgmresInfo(ctypes.Structure):
@@ -308,7 +308,7 @@ def hec_to_csr(matrix, levels=None, stream=None):
 def sptrsv_plan_create(matrix, levels, max_nrhs=1, block_threads=0, blocks_per_sm=0, wait_cycles=0,
                        debug_unpublished_row=None, backoff_ns=0, lanes_per_row=0):
     t = HecTune(block_threads, blocks_per_sm, wait_cycles,
-                0 if debug_unpublished_row is None else int(debug_unpublished_row) + 1, backoff_ns, lanes_per_row)
+                0 if debug_unpublished_row is None else int(debug_unpublished_row) + 1, backoff_ns, lanes_per_row, 0)
     out = _vp()
     _check(_sptrsv_plan_create(matrix.h, levels.h, int(max_nrhs), ctypes.byref(t), ctypes.byref(out)), "sptrsv_plan_create")
     return Plan(out.value, keep=(matrix, levels))
@@ -346,7 +346,8 @@ def sptrsv_autotune(plan, nrhs=1, stream=None):
     """Times the plan's sweep over candidate launch shapes and keeps the fastest; returns it."""
     t = HecTune()
     _check(_sptrsv_autotune(plan.h, int(nrhs), ctypes.byref(t), _stream(stream)), "sptrsv_autotune")
-    return dict(block_threads=t.block_threads, blocks_per_sm=t.blocks_per_sm, lanes_per_row=t.lanes_per_row)
+    return dict(block_threads=t.block_threads, blocks_per_sm=t.blocks_per_sm, lanes_per_row=t.lanes_per_row,
+                partitioned=bool(t.partitioned))
 
 
 def sptrsv_lower(plan, b, x=None, stream=None):
