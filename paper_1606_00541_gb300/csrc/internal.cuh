@@ -137,7 +137,8 @@ struct ilu_precond {
     int* l_gather = nullptr;   // [n_ext] lower sweep: new row -> row of r to read
     int* l_scatter = nullptr;  // [n_ext] lower sweep: new row -> row of the intermediate y (in U order)
     int* u_scatter = nullptr;  // [n_ext] upper sweep: new row -> row of z to write, -1 = not owned
-    double* y = nullptr;       // [n_ext * max_nrhs] intermediate, already in the upper factor's order
+    void* y = nullptr;         // [n_ext * max_nrhs] intermediate, already in the upper factor's order
+    bool y32 = false;          // y in FP32 (both sweeps compute in FP32), else FP64
     int max_nrhs = 1;
 };
 
@@ -182,7 +183,7 @@ inline int default_lanes_per_row(const hec_matrix* T) {
 // sweep launcher shared by sptrsv_* and ilu_apply: gather[r] is the row of b feeding new row r
 // (NULL = identity), scatter[r] the row of x receiving it (NULL = identity, -1 = skip).
 hec_status sweep(const sptrsv_plan* p, int nrhs, const double* b, int ldb, const int* gather, double* x,
-                 int ldx, const int* scatter, cudaStream_t s);
+                 int ldx, const int* scatter, cudaStream_t s, bool b32 = false, bool x32 = false);
 // y = alpha A x + beta y for a general-mode FP64 HEC matrix (krylov.cu; no argument checks)
 hec_status spmv_impl(const hec_matrix* A, int K, double alpha, const double* x, int ldx, double beta, double* y,
                      int ldy, cudaStream_t s);

@@ -47,7 +47,19 @@ struct SweepParams {
     const int2* __restrict__ chunks;  // (first row, rows) of each level-aligned chunk
     int nchunks;
     const void* __restrict__ dinv;     // reciprocal diagonal in the work type (NULL: divide)
+    int b32, x32;                      // b / x hold FP32 values (the ILU apply's intermediate)
 };
+
+// The right-hand side read and the solution written by a sweep: FP64 at the boundary, FP32 for
+// the intermediate y of an ILU apply with FP32 / BF16 factor values (it only feeds the upper
+// sweep, which computes in FP32, so keeping it in FP32 changes no result).
+template <typename AT> __device__ __forceinline__ AT ld_rhs(const double* b, int b32, long i) {
+    return b32 ? (AT)__ldg((const float*)b + i) : (AT)__ldg(b + i);
+}
+template <typename AT> __device__ __forceinline__ void st_sol(double* x, int x32, long i, AT v) {
+    if (x32) ((float*)x)[i] = (float)v;
+    else x[i] = (double)v;
+}
 
 template <typename XT> struct Acc { typedef float T; };
 template <> struct Acc<double> { typedef double T; };
@@ -57,6 +69,9 @@ template <> __device__ __forceinline__ float ldv<__nv_bfloat16, float>(const __n
     return __bfloat162float(__ldg(p));
 }
 
+// a stored value widened to the work type (no load)
+template <typename VT, typename AT> __device__ __forceinline__ AT widen_v(VT v) { return (AT)v; }
+template <> __device__ __forceinline__ float widen_v<__nv_bfloat16, float>(__nv_bfloat16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ double wait_x(const double* p, int* st, long long b) { return wait_f64(p, st, b); }
 __device__ __forceinline__ float wait_x(const float* p, int* st, long long b) { return wait_f32(p, st, b); }
 __device__ __forceinline__ void publish_x(double* p, double v) { publish_f64(p, v); }
@@ -199,7 +214,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepParams p) {
         int t0 = 0, tl = 0, sr = -1;
         if (act) {
             const int gr = p.gather ? __ldg(p.gather + r) : r;
-            acc = (AT)__ldg(p.b + (long)gr * p.ldb + q);
+            acc = ld_rhs<AT>(p.b, p.b32, (long)gr * p.ldb + q);
             t0 = __ldg(p.tptr + r);
             const int t1 = __ldg(p.tptr + r + 1) - 1;
             tl = t1 - t0;
@@ -255,7 +270,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepParams p) {
         if (act) {
             const AT xr = p.dinv ? acc * diag : acc / diag;
             if (r != p.skip_row) publish_x(xp + (long)r * K + q, (XT)xr);
-            if (sr >= 0) p.x[(long)sr * p.ldx + q] = (double)xr;
+            if (sr >= 0) st_sol(p.x, p.x32, (long)sr * p.ldx + q, xr);
         }
     }
 }
@@ -292,7 +307,7 @@ __global__ void __launch_bounds__(256) k_sweep_lpr(SweepParams p) {
             tl = t1 - t0;
             if (sub == 0) {
                 const int gr = p.gather ? __ldg(p.gather + r) : r;
-                acc = (AT)__ldg(p.b + (long)gr * p.ldb);
+                acc = ld_rhs<AT>(p.b, p.b32, (long)gr * p.ldb);
                 diag = p.dinv ? (AT)__ldg((const XT*)p.dinv + r) : ldv<VT, AT>(tv + t1);
                 sr = p.scatter ? __ldg(p.scatter + r) : r;
             }
@@ -353,7 +368,7 @@ __global__ void __launch_bounds__(256) k_sweep_lpr(SweepParams p) {
         if (act && sub == 0) {
             const AT xr = p.dinv ? acc * diag : acc / diag;
             if (r != p.skip_row) publish_x(xp + r, (XT)xr);
-            if (sr >= 0) p.x[(long)sr * p.ldx] = (double)xr;
+            if (sr >= 0) st_sol(p.x, p.x32, (long)sr * p.ldx, xr);
         }
     }
 }
@@ -460,12 +475,58 @@ struct DepBatchV {
     }
 };
 
+// One lane's share of a row of a chunk of the multi-right-hand-side sweep, everything but the
+// dependencies' values: its G right-hand sides (gathered through p.gather), the reciprocal
+// diagonal (the diagonal itself when the plan has none), the tail range, the scatter row and the
+// first WMAX slab slots.  Loaded for the warp's
+// next chunk while it works on the current one, so a chunk's HBM loads overlap the wait of the
+// chunk before it.
+template <typename VT, typename XT, typename AT, int G, int WMAX>
+struct VecRow {
+    AT b[G];
+    AT d;
+    int t0, tl, sr;
+    int cc[WMAX];
+    VT v[WMAX];
+    __device__ __forceinline__ void load(const SweepParams& p, int2 ch, int rsub, int q0) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) b[g] = AT(0);
+        d = AT(1);
+        t0 = tl = 0;
+        sr = -1;
+#pragma unroll
+        for (int k = 0; k < WMAX; ++k) {
+            cc[k] = -1;
+            v[k] = VT(0.0f);
+        }
+        if (rsub < ch.y) {
+            const int r = ch.x + rsub;
+            const int gr = p.gather ? __ldg(p.gather + r) : r;
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+                if (q0 + g < p.K) b[g] = ld_rhs<AT>(p.b, p.b32, (long)gr * p.ldb + q0 + g);
+            t0 = __ldg(p.tptr + r);
+            const int t1 = __ldg(p.tptr + r + 1) - 1;
+            tl = t1 - t0;
+            d = p.dinv ? (AT)__ldg((const XT*)p.dinv + r) : ldv<VT, AT>((const VT*)p.tval + t1);
+            sr = p.scatter ? __ldg(p.scatter + r) : r;
+#pragma unroll
+            for (int k = 0; k < WMAX; ++k) {
+                if (k < p.w) {
+                    const long s = (long)k * p.ld + r;
+                    cc[k] = __ldg(p.ell_col + s);
+                    v[k] = __ldg((const VT*)p.ell_val + s);
+                }
+            }
+        }
+    }
+};
+
 template <typename VT, typename XT, int LPR, int G, int WMAX>
 __global__ void __launch_bounds__(256) k_sweep_vec(SweepParams p) {
     typedef typename Acc<XT>::T AT;
     typedef Word<XT> W;
     constexpr int KS = LPR * G;   // padded row stride of the level-ordered solution
-    constexpr int RPW = 32 / LPR;  // rows per warp step
     const int lane = threadIdx.x & 31;
     const int rsub = lane / LPR, q0 = (lane % LPR) * G;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -474,37 +535,29 @@ __global__ void __launch_bounds__(256) k_sweep_vec(SweepParams p) {
     const VT* __restrict__ tv = (const VT*)p.tval;
     XT* xp = (XT*)p.xp;
     const int K = p.K;
-    (void)RPW;
+    // chunk entries run two chunks ahead of the warp, row data one chunk ahead
+    int2 ch_a = gw < p.nchunks ? __ldg(p.chunks + gw) : make_int2(0, 0);
+    int2 ch_b = gw + nw < p.nchunks ? __ldg(p.chunks + gw + nw) : make_int2(0, 0);
+    VecRow<VT, XT, AT, G, WMAX> nxt, row;
+    nxt.load(p, ch_a, rsub, q0);
     for (int c = gw; c < p.nchunks; c += nw) {
-        const int2 ch = __ldg(p.chunks + c);
+        const int2 ch = ch_a;
+        ch_a = ch_b;
+        if (c + 2 * nw < p.nchunks) ch_b = __ldg(p.chunks + c + 2 * nw);
+        row = nxt;
+        nxt.load(p, c + nw < p.nchunks ? ch_a : make_int2(0, 0), rsub, q0);
         const int r = ch.x + rsub;
         const bool act = rsub < ch.y;
         AT acc[G];
-        AT diag = AT(1);
-        int t0 = 0, tl = 0, sr = -1;
 #pragma unroll
-        for (int g = 0; g < G; ++g) acc[g] = AT(0);
-        if (act) {
-            const int gr = p.gather ? __ldg(p.gather + r) : r;
-#pragma unroll
-            for (int g = 0; g < G; ++g)
-                if (q0 + g < K) acc[g] = (AT)__ldg(p.b + (long)gr * p.ldb + q0 + g);
-            t0 = __ldg(p.tptr + r);
-            const int t1 = __ldg(p.tptr + r + 1) - 1;
-            tl = t1 - t0;
-            diag = p.dinv ? (AT)__ldg((const XT*)p.dinv + r) : ldv<VT, AT>(tv + t1);
-            sr = p.scatter ? __ldg(p.scatter + r) : r;
-        }
+        for (int g = 0; g < G; ++g) acc[g] = row.b[g];
+        const AT diag = row.d;
+        const int t0 = row.t0, tl = row.tl, sr = row.sr;
         DepBatchV<XT, AT, WMAX, G> slab;
         slab.clear(xp);
 #pragma unroll
-        for (int k = 0; k < WMAX; ++k) {
-            if (act && k < p.w) {
-                const long s = (long)k * p.ld + r;
-                const int cc = __ldg(p.ell_col + s);
-                if (cc >= 0) slab.set(k, xp + (long)cc * KS + q0, ldv<VT, AT>(ev + s));
-            }
-        }
+        for (int k = 0; k < WMAX; ++k)
+            if (act && row.cc[k] >= 0) slab.set(k, xp + (long)row.cc[k] * KS + q0, widen_v<VT, AT>(row.v[k]));
         slab.poll();
         slab.wait(p.status, p.budget, p.backoff_ns);
         slab.accumulate(acc);
@@ -558,7 +611,7 @@ __global__ void __launch_bounds__(256) k_sweep_vec(SweepParams p) {
             if (sr >= 0)
 #pragma unroll
                 for (int g = 0; g < G; ++g)
-                    if (q0 + g < K) p.x[(long)sr * p.ldx + q0 + g] = (double)xr[g];
+                    if (q0 + g < K) st_sol(p.x, p.x32, (long)sr * p.ldx + q0 + g, xr[g]);
         }
     }
 }
@@ -597,6 +650,7 @@ struct PartParams {
     int* status;
     long long budget;
     int skip_row;
+    int b32, x32;  // b / x hold FP32 values (the ILU apply's intermediate)
 };
 
 // Volatile shared-memory word loads by shared-window address, so a local poll is always a
@@ -721,8 +775,6 @@ struct DepBatchP {
 // here uses a loaded value: widening, the tail length and the scatter index are derived when the
 // chunk is processed, so issuing the prefetch never stalls the warp.  Slab values are loaded
 // whether or not the slot is padding (padding is in bounds and zero).
-template <typename VT, typename AT> __device__ __forceinline__ AT widen_v(VT v) { return (AT)v; }
-template <> __device__ __forceinline__ float widen_v<__nv_bfloat16, float>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 template <typename VT, typename XT, typename AT, int NP>
 struct PartRow {
@@ -749,7 +801,7 @@ struct PartRow {
                 b = __ldg((const AT*)p.bp + r);
             } else {  // FP64: gathered here (the row is loaded when its chunk starts)
                 const int gr = p.gather ? __ldg(p.gather + g) : g;
-                b = (AT)__ldg(p.b + (long)gr * p.ldb);
+                b = ld_rhs<AT>(p.b, p.b32, (long)gr * p.ldb);
             }
             t0 = __ldg(p.tptr + r);
             t1 = __ldg(p.tptr + r + 1);
@@ -770,14 +822,14 @@ struct PartRow {
 // side gathered into plan order in the work type.
 template <typename XT>
 __global__ void k_part_prep(int n, XT* xp, const int* __restrict__ rowg, const int* __restrict__ gather,
-                            const double* __restrict__ b, int ldb, typename Acc<XT>::T* bp) {
+                            const double* __restrict__ b, int ldb, int b32, typename Acc<XT>::T* bp) {
     const int st = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) {
         if (sizeof(XT) == 8) ((unsigned long long*)xp)[i] = kSent64;
         else ((unsigned int*)xp)[i] = kSent32;
         const int g = __ldg(rowg + i);
         const int gr = gather ? __ldg(gather + g) : g;
-        bp[i] = (typename Acc<XT>::T)__ldg(b + (long)gr * ldb);
+        bp[i] = ld_rhs<typename Acc<XT>::T>(b, b32, (long)gr * ldb);
     }
 }
 
@@ -878,7 +930,7 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_part(PartParams p) {
             *(volatile WT*)(sxp + (r - lo)) = wv;  // consumers in this part
         }
         if (pub) publish_x(xp + r, (XT)xr);  // consumers in other parts
-        if (act && sr >= 0) p.x[(long)sr * p.ldx] = (double)xr;
+        if (act && sr >= 0) st_sol(p.x, p.x32, (long)sr * p.ldx, xr);
     }
 }
 
@@ -1106,7 +1158,7 @@ hec_status launch_part(const sptrsv_plan* pl, PartParams& pp, cudaStream_t s) {
     {
         ProfScope ps_(s, PROF_FILL);
         if (sizeof(typename Acc<XT>::T) == 4)
-            k_part_prep<XT><<<fb, 256, 0, s>>>((int)count, (XT*)pp.xp, P->rowg, pp.gather, pp.b, pp.ldb,
+            k_part_prep<XT><<<fb, 256, 0, s>>>((int)count, (XT*)pp.xp, P->rowg, pp.gather, pp.b, pp.ldb, pp.b32,
                                                (typename Acc<XT>::T*)P->bp);
         else
             k_fill_sentinel<XT><<<fb, 256, 0, s>>>((XT*)pp.xp, count);
@@ -1135,7 +1187,7 @@ const void* part_kernel(int w) {
 }  // namespace
 
 hec_status sweep(const sptrsv_plan* pl, int nrhs, const double* b, int ldb, const int* gather, double* x, int ldx,
-                 const int* scatter, cudaStream_t s) {
+                 const int* scatter, cudaStream_t s, bool b32, bool x32) {
     const hec_matrix* T = pl->T;
     if (T->n == 0) return HEC_OK;
     if (pl->part && pl->use_part && nrhs == 1) {
@@ -1165,6 +1217,8 @@ hec_status sweep(const sptrsv_plan* pl, int nrhs, const double* b, int ldb, cons
         pp.status = pl->status;
         pp.budget = pl->wait_cycles;
         pp.skip_row = pl->skip_row;
+        pp.b32 = b32;
+        pp.x32 = x32;
         switch (T->vdt) {
             case HEC_F64: return dispatch_part<double, double>(pl, pp, s);
             case HEC_F32: return dispatch_part<float, float>(pl, pp, s);
@@ -1193,6 +1247,8 @@ hec_status sweep(const sptrsv_plan* pl, int nrhs, const double* b, int ldb, cons
     sp.skip_row = pl->skip_row;
     sp.backoff_ns = pl->backoff_ns;
     sp.dinv = pl->dinv;
+    sp.b32 = b32;
+    sp.x32 = x32;
     switch (T->vdt) {
         case HEC_F64: return dispatch_w<double, double>(pl, sp, s);
         case HEC_F32: return dispatch_w<float, float>(pl, sp, s);
@@ -1719,9 +1775,12 @@ HEC_API hec_status ilu_create(const sptrsv_plan* L, const sptrsv_plan* U, int n_
     M->n_glob = n_glob;
     M->n_ext = n_ext;
     M->max_nrhs = std::min(L->max_nrhs, U->max_nrhs);
+    // the intermediate y in FP32 when both sweeps compute in FP32 (FP32 / BF16 values)
+    M->y32 = L->T->vdt != HEC_F64 && U->T->vdt != HEC_F64;
     hec_status st = HEC_OK;
     if ((st = dalloc(&M->l_gather, (size_t)n_ext)) || (st = dalloc(&M->l_scatter, (size_t)n_ext)) ||
-        (st = dalloc(&M->u_scatter, (size_t)n_ext)) || (st = dalloc(&M->y, (size_t)n_ext * M->max_nrhs))) {
+        (st = dalloc(&M->u_scatter, (size_t)n_ext)) ||
+        (st = dmalloc(&M->y, (M->y32 ? sizeof(float) : sizeof(double)) * (size_t)n_ext * M->max_nrhs + 16))) {
         ilu_destroy(M);
         return st;
     }
@@ -1756,7 +1815,7 @@ HEC_API hec_status ilu_apply(const ilu_precond* M, int nrhs, const double* r, in
         return set_error(HEC_ERR_INVALID_ARG, "ilu_apply: bad argument");
     cudaStream_t s = S(stream);
     // L y = r: gather r, write y already permuted into the upper factor's level order
-    HEC_CHECK(sweep(M->L, nrhs, r, ldr, M->l_gather, M->y, nrhs, M->l_scatter, s));
+    HEC_CHECK(sweep(M->L, nrhs, r, ldr, M->l_gather, (double*)M->y, nrhs, M->l_scatter, s, false, M->y32));
     // U z = y: y is read in order, z is written back (owned rows only for RAS)
-    return sweep(M->U, nrhs, M->y, nrhs, nullptr, z, ldz, M->u_scatter, s);
+    return sweep(M->U, nrhs, (const double*)M->y, nrhs, nullptr, z, ldz, M->u_scatter, s, M->y32, false);
 }
