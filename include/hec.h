@@ -231,6 +231,18 @@ int sptrsv_partition_capacity(const sptrsv_plan* p, int threads);
  * counterpart. */
 hec_status sptrsv_autotune(sptrsv_plan* p, int nrhs, hec_tune* out, void* stream);
 
+/* Checks, on the device, every index the sweep kernels follow without a bounds check (a check per
+ * gathered index would sit on the dependency chain), so that a plan whose arrays were corrupted
+ * is reported instead of swept: the level map (perm and iperm inverse permutations, level_ptr
+ * from 0 to n); the HEC factor (tail row pointers increasing from 0 to tail_nnz, slab columns in
+ * [-1, n) with padding only after a row's entries, tail off-diagonals only after a full slab,
+ * every off-diagonal in an earlier level than its row, the diagonal last in the tail and
+ * nonzero); every chunk table (in order, each chunk inside one level, covering [0, n)); and, for a
+ * partitioned plan, the row map (a permutation), the part tables, the repacked factor and the
+ * part chunks.  Returns HEC_OK, or HEC_ERR_OUT_OF_BOUNDS with hec_last_error() naming the first
+ * failing check and index.  Reads only the plan; synchronizes `stream`. */
+hec_status sptrsv_plan_check(const sptrsv_plan* p, void* stream);
+
 /* Reads and clears the device status word of a plan (synchronizes `stream`).  Returns HEC_OK,
  * HEC_ERR_TIMEOUT or HEC_ERR_OUT_OF_BOUNDS as recorded by the kernels since the last call. */
 hec_status hec_sync_status(const sptrsv_plan* p, void* stream);

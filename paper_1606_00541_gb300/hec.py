@@ -358,6 +358,15 @@ def sptrsv_upper(plan, b, x=None, stream=None):
     return _solve(_sptrsv_upper, "sptrsv_upper", plan, b, x, stream)
 
 
+_sptrsv_plan_check = _sig("sptrsv_plan_check", _vp, _vp)
+
+
+def sptrsv_plan_check(plan, stream=None):
+    """Device-side check of every index the sweeps follow (include/hec.h); raises HecError
+    (OUT_OF_BOUNDS) naming the first failing check."""
+    _check(_sptrsv_plan_check(plan.h, _stream(stream)), "sptrsv_plan_check")
+
+
 def hec_sync_status(plan, stream=None):
     return _hec_sync_status(plan.h, _stream(stream))
 
