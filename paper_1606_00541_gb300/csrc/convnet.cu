@@ -15,8 +15,11 @@
 // same kernel run with the spatially flipped, channel-transposed weights and the ReLU mask of
 // the layer applied while the halo is staged; the weight gradient is a GEMM over voxels with
 // per-block partial sums reduced in a fixed order (deterministic).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <string>
 #include <vector>
 
 #include "internal.cuh"
@@ -301,6 +304,295 @@ __global__ void __launch_bounds__(kConvThreads, 4)
     }
 }
 
+// ---- the 16 -> 16 (and 16 -> 1) forward convolution on the 5th-generation tensor cores ---------
+// Implicit GEMM with tcgen05.mma (kind::f16: BF16 operands, FP32 accumulators in tensor memory),
+// streamed along z.  A work item is a strip of output voxels 128 (x) x TCY (y) x up to TCZ (z);
+// the CTA walks the item's input planes z0-1 .. z0+zc.  One input plane's slab (its TCY+2 rows of
+// 130 voxels, x0-1 .. x0+128, 32 bytes each) is brought into shared memory by one TMA load
+// (voxels outside the grid or the sample read as zeros) and multiplied, for every output row y and tap (dy, dx), by the three dz taps at once: one MMA of
+// M = 128 voxels, N = 48 = 3 dz x 16 output channels, K = 16 input channels whose three 16-column
+// groups land in the accumulators of output planes z_in+1, z_in, z_in-1.  The accumulators of an
+// item's planes sit in TMEM in descending z order (per output row), so those three are
+// contiguous; at the ends of the chunk N drops to 32 or 16.  Each input voxel row is therefore
+// read by 9 MMAs per output row instead of 27.
+//   Operand layout (K-major): A's rows are the slab's voxels, 32 bytes (16 channels) each, in the
+// 32-byte swizzle the TMA load writes (the two 16-byte halves of a row swapped where bit 7 of its
+// shared-memory address is set; 8-row groups 256 bytes apart).  The swizzle follows the absolute
+// address, so a tap's shift (dy rows of 130 voxels, dx voxels) is an offset of the start address.
+// B for tap (dy, dx), unswizzled: rows dz*16 + co (16 bytes apart), its channel halves 768 bytes
+// apart.
+//   Warp roles: warp 4 issues the TMA loads into a ring of TC_RING slabs, warp 5 issues the MMAs
+// (one thread), warps 0-3 drain finished planes (warp w reads TMEM lanes 32w .. 32w+31, i.e.
+// voxels x0 + 32w ..), add the bias, apply the ReLU, round to BF16 and zero the accumulator for
+// its next use.  mbarriers link the roles: slab full (TMA bytes) / slab free (MMA commit), plane
+// finished (MMA commit) / plane drained (the four epilogue warps).  Every wait is bounded: one
+// that runs out sets the kernel's abort flag and the status word, all roles leave their loops,
+// the loads and MMAs already issued are waited for (bounded) and the TMEM is freed.
+constexpr int TCX = 128, TCY = 2, TCZ = 8, TC_RING = 5;
+constexpr int TC_HX = TCX + 2, TC_HY = TCY + 2;
+constexpr int TC_SLAB = TC_HY * TC_HX * 32;               // one TMA box: 16,640 bytes (65 x 256)
+constexpr int TC_WBLK = 3 * C * C * 2;                     // B of one (dy, dx): 48 rows x 16 channels
+constexpr int TC_SMEM = TC_RING * TC_SLAB + 9 * TC_WBLK;   // 97,024 bytes: two CTAs per SM
+constexpr int TC_COLS = TCY * TCZ * 16;                    // 256 TMEM columns per CTA
+constexpr int kTcThreads = 192;
+constexpr long long kTcWaitBudget = 2000000000LL;          // clock cycles (about 1 s)
+
+// shared-memory matrix descriptors (version 1, base offset 0).  tc_desc: K-major, no swizzle,
+// 8-row groups 128 bytes apart, the two 8-element halves of K `lbo` bytes apart.  tc_desc_sw32:
+// K-major, 32-byte swizzle (mode 6), rows of 32 bytes, 8-row groups 256 bytes apart.
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr, unsigned lbo) {
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((128u >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ unsigned long long tc_desc_sw32(unsigned addr) {
+    return (unsigned long long)((addr >> 4) & 0x3FFFu) | (1ull << 16) | ((unsigned long long)(256u >> 4) << 32) |
+           (1ull << 46) | (6ull << 61);
+}
+__device__ __forceinline__ bool mbar_try(unsigned mb, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(mb), "r"(parity) : "memory");
+    return ok != 0;
+}
+// wait for the phase of parity `parity`; false when the budget ran out (sets *abort) or another
+// role aborted
+__device__ __forceinline__ bool mbar_wait(unsigned mb, unsigned parity, volatile int* abort) {
+    const long long t0 = clock64();
+    for (unsigned it = 0;; ++it) {
+        if (mbar_try(mb, parity)) return true;
+        if ((it & 63u) == 63u) {
+            if (*abort) return false;
+            if (clock64() - t0 > kTcWaitBudget) {
+                *abort = 1;
+                return false;
+            }
+        }
+    }
+}
+// the same wait on the way out: ignores the abort flag, gives up after the budget
+__device__ __forceinline__ void mbar_drain(unsigned mb, unsigned parity) {
+    const long long t0 = clock64();
+    for (unsigned it = 0; !mbar_try(mb, parity); ++it)
+        if ((it & 63u) == 63u && clock64() - t0 > kTcWaitBudget) return;
+}
+__device__ __forceinline__ void tc_commit(unsigned mb) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
+}
+
+struct TcItem {
+    int x0, y0, z0, zc, sample;
+};
+__device__ __forceinline__ TcItem tc_item(int i, int xt, int yt, int zt, int zs) {
+    TcItem t;
+    t.x0 = (i % xt) * TCX;
+    i /= xt;
+    t.y0 = (i % yt) * TCY;
+    i /= yt;
+    t.z0 = (i % zt) * TCZ;
+    t.sample = i / zt;
+    t.zc = min(TCZ, zs - t.z0);
+    return t;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(kTcThreads, 2)
+    k_conv_tc(Geom g, int xt, int yt, int zt, int nitems, const __grid_constant__ CUtensorMap tmap,
+              const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias, int relu, ConvOut out, int* status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long bar_full[TC_RING], bar_free[TC_RING], bar_done[TCZ], bar_drained[TCZ],
+        bar_fin;
+    __shared__ unsigned tmem_slot;
+    __shared__ int abort_flag;
+    volatile int* abort = &abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned sh = (unsigned)__cvta_generic_to_shared(smem);
+    const unsigned sw = sh + TC_RING * TC_SLAB;
+    auto bar = [](unsigned long long* b) { return (unsigned)__cvta_generic_to_shared(b); };
+
+    // B blocks: tap (dy, dx) = j, row n = dz*16 + co, half h -> sw + j*1536 + h*768 + n*16
+    for (int i = tid; i < 9 * 48 * 2; i += kTcThreads) {
+        const int h = i & 1, n = (i >> 1) % 48, j = (i >> 1) / 48;
+        const int tap = (n >> 4) * 9 + j, co = n & 15;
+        cp_async16(sw + j * TC_WBLK + h * (TC_WBLK / 2) + n * 16, W + ((long)tap * C + co) * C + h * 8, 16);
+    }
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < TC_RING; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(&bar_full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(&bar_free[s])));
+        }
+        for (int k = 0; k < TCZ; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(&bar_done[k])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(bar(&bar_drained[k])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(&bar_fin)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(&tmem_slot)),
+                     "n"(TC_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the tensor cores read the B blocks
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = tmem_slot;
+    if (warp < 4) {
+        // all accumulators start at zero; the MMAs always accumulate
+        const unsigned z = 0u;
+        for (int c = 0; c < TC_COLS; c += 16)
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};"
+                         ::"r"(tmem + ((unsigned)(warp * 32) << 16) + c), "r"(z) : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    if (warp == 4) {
+        // ---- TMA producer ----
+        if (lane == 0) {
+            int it = 0;
+            const unsigned long long tm = reinterpret_cast<unsigned long long>(&tmap);
+            for (int i = blockIdx.x; i < nitems && !*abort; i += gridDim.x) {
+                const TcItem t = tc_item(i, xt, yt, zt, g.zs);
+                for (int p = 0; p <= t.zc + 1; ++p, ++it) {
+                    const int s = it % TC_RING, use = it / TC_RING;
+                    if (use > 0 && !mbar_wait(bar(&bar_free[s]), (use - 1) & 1, abort)) break;
+                    const unsigned fb = bar(&bar_full[s]);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "n"(TC_SLAB) : "memory");
+                    asm volatile(
+                        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                        "%4, %5, %6}], [%7];" ::"r"(sh + s * TC_SLAB), "l"(tm), "r"(0), "r"(t.x0 - 1), "r"(t.y0 - 1),
+                        "r"(t.z0 - 1 + p), "r"(t.sample), "r"(fb)
+                        : "memory");
+                }
+                if (*abort) break;
+            }
+            // the loads already issued land before the CTA ends (each slab's last fill)
+            for (int k = it - 1; k >= 0 && k >= it - TC_RING; --k) mbar_drain(bar(&bar_full[k % TC_RING]), (k / TC_RING) & 1);
+        }
+    } else if (warp == 5) {
+        // ---- MMA issuer ----
+        if (lane == 0) {
+            const unsigned base_idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TCX >> 4) << 24);
+            unsigned used = 0, wpar = 0;  // per accumulator plane: used by an earlier item, next drained parity
+            int it = 0;
+            bool issued = false;
+            for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+                const TcItem t = tc_item(i, xt, yt, zt, g.zs);
+                bool ok = true;
+                for (int p = 0; p <= t.zc + 1 && ok; ++p, ++it) {
+                    const int s = it % TC_RING;
+                    if (!mbar_wait(bar(&bar_full[s]), (it / TC_RING) & 1, abort)) { ok = false; break; }
+                    if (p < t.zc && ((used >> p) & 1u)) {  // plane p is written first now: drained?
+                        if (!mbar_wait(bar(&bar_drained[p]), (wpar >> p) & 1u, abort)) { ok = false; break; }
+                        wpar ^= 1u << p;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const int dz_lo = max(0, p - t.zc + 1), dz_hi = min(2, p);
+                    const int nn = (dz_hi - dz_lo + 1) * 16;
+                    const unsigned idesc = base_idesc | ((unsigned)(nn >> 3) << 17);
+                    const int kcol = (TCZ - 1 - (p - dz_lo)) * 16;  // first column: plane p - dz_lo
+                    const unsigned slab = sh + s * TC_SLAB;
+#pragma unroll
+                    for (int y = 0; y < TCY; ++y)
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                            for (int dx = 0; dx < 3; ++dx) {
+                                const unsigned long long ad = tc_desc_sw32(slab + ((y + dy) * TC_HX + dx) * 32);
+                                const unsigned long long bd =
+                                    tc_desc(sw + (dy * 3 + dx) * TC_WBLK + dz_lo * 256, TC_WBLK / 2);
+                                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, 1, 0;\n"
+                                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                             ::"r"(tmem + y * (TCZ * 16) + kcol), "l"(ad), "l"(bd), "r"(idesc));
+                            }
+                    issued = true;
+                    tc_commit(bar(&bar_free[s]));                 // the slab may be refilled once these finish
+                    if (p >= 2) tc_commit(bar(&bar_done[p - 2]));  // plane p-2 has all its contributions
+                    if (p < t.zc) used |= 1u << p;
+                }
+                if (!ok) break;
+            }
+            if (issued) {  // every MMA issued has finished before the TMEM is freed
+                tc_commit(bar(&bar_fin));
+                mbar_drain(bar(&bar_fin), 0);
+            }
+        }
+    } else {
+        // ---- epilogue: warps 0-3 ----
+        float bv[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) bv[c] = bias ? bias[c] : 0.f;
+        unsigned dpar = 0;
+        const unsigned lane_base = tmem + ((unsigned)(warp * 32) << 16);
+        bool ok = true;
+        for (int i = blockIdx.x; i < nitems && ok; i += gridDim.x) {
+            const TcItem t = tc_item(i, xt, yt, zt, g.zs);
+            const int x = t.x0 + warp * 32 + lane;
+            for (int k = 0; k < t.zc; ++k) {
+                ok = __all_sync(0xffffffffu, mbar_wait(bar(&bar_done[k]), (dpar >> k) & 1u, abort));
+                if (!ok) break;
+                dpar ^= 1u << k;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const int z = t.z0 + k;
+#pragma unroll
+                for (int y = 0; y < TCY; ++y) {
+                    const unsigned ta = lane_base + y * (TCZ * 16) + (TCZ - 1 - k) * 16;
+                    unsigned r[16];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                        : "r"(ta));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    const unsigned zr = 0u;
+                    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};"
+                                 ::"r"(ta), "r"(zr) : "memory");
+                    const int yy = t.y0 + y;
+                    if (x >= g.nx || yy >= g.ny) continue;
+                    const long vox = (((long)t.sample * g.zs + z) * g.ny + yy) * g.nx + x;
+                    float v[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        v[c] = __uint_as_float(r[c]) + bv[c];
+                        if (relu) v[c] = fmaxf(v[c], 0.f);
+                    }
+                    if (out.Y) {
+                        uint4 lo, hi = make_uint4(0u, 0u, 0u, 0u);  // one output channel: channels 8-15 stored as zeros
+                        lo.x = pack2(__float2bfloat16_rn(v[0]), __float2bfloat16_rn(v[1]));
+                        lo.y = pack2(__float2bfloat16_rn(v[2]), __float2bfloat16_rn(v[3]));
+                        lo.z = pack2(__float2bfloat16_rn(v[4]), __float2bfloat16_rn(v[5]));
+                        lo.w = pack2(__float2bfloat16_rn(v[6]), __float2bfloat16_rn(v[7]));
+                        if (NT == 2) {
+                            hi.x = pack2(__float2bfloat16_rn(v[8]), __float2bfloat16_rn(v[9]));
+                            hi.y = pack2(__float2bfloat16_rn(v[10]), __float2bfloat16_rn(v[11]));
+                            hi.z = pack2(__float2bfloat16_rn(v[12]), __float2bfloat16_rn(v[13]));
+                            hi.w = pack2(__float2bfloat16_rn(v[14]), __float2bfloat16_rn(v[15]));
+                        }
+                        ((uint4*)(out.Y + vox * C))[0] = lo;
+                        ((uint4*)(out.Y + vox * C))[1] = hi;
+                    }
+                    if (out.Y0) out.Y0[vox] = v[0] * out.y0_scale;
+                    if (out.Yd) out.Yd[vox] = *out.yd_scale * (double)(v[0] * out.y0_scale);
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(&bar_drained[k])) : "memory");
+            }
+        }
+    }
+    if (*abort && tid == 0 && status) atomicCAS(status, 0, HEC_ERR_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 5) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TC_COLS));
+}
+
 // Weight and bias gradients of one layer: partial[block][tap][ci][co] = sum over this tile's voxels
 // of Ain[v + off(tap)][ci] * dZ[v][co], partial[block][WSZ + co] = sum of dZ[v][co];
 // dZ = dA masked by the layer's ReLU (mask = its output) when mask is given.
@@ -458,6 +750,8 @@ struct hec_net {
     float* partial = nullptr;
     long partial_cap = 0;
     float* lpart = nullptr;
+    int tensor_cores = 1;              // forward 16-channel layers on tcgen05 (else mma.sync)
+    int* status = nullptr;             // device word: HEC_ERR_TIMEOUT if a tensor-core wait ran out
 };
 
 namespace hec {
@@ -468,7 +762,7 @@ void free_net(hec_net* N) {
     cudaFree(N->P); cudaFree(N->G); cudaFree(N->M); cudaFree(N->V); cudaFree(N->Wf); cudaFree(N->Wd); cudaFree(N->Wx);
     for (auto& a : N->act) cudaFree(a);
     for (auto& a : N->dA) cudaFree(a);
-    cudaFree(N->out); cudaFree(N->partial); cudaFree(N->lpart);
+    cudaFree(N->out); cudaFree(N->partial); cudaFree(N->lpart); cudaFree(N->status);
     delete N;
 }
 
@@ -528,6 +822,50 @@ hec_status conv(const Geom& g, const ConvIn& in, const __nv_bfloat16* W, const f
     return HEC_OK;
 }
 
+// the 16-input-channel forward convolution on the tensor cores (see k_conv_tc)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+template <int NT>
+hec_status conv_tc(const Geom& g, const __nv_bfloat16* X, const __nv_bfloat16* W, const float* bias, int relu,
+                   const ConvOut& out, int* status, cudaStream_t s) {
+    static bool smem_set = false;
+    if (!smem_set) {
+        HEC_CUDA(cudaFuncSetAttribute(k_conv_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+        smem_set = true;
+    }
+    auto encode = tensor_map_encoder();
+    if (!encode) return set_error(HEC_ERR_CUDA, "net: cuTensorMapEncodeTiled is not available");
+    // X viewed as [sample][z][y][x][16 channels]; a box is 130 voxels x (TCY+2) rows of one plane,
+    // written to shared memory in the 32-byte swizzle
+    const cuuint64_t row = 32, nx = (cuuint64_t)g.nx, ny = (cuuint64_t)g.ny, zs = (cuuint64_t)g.zs;
+    const cuuint64_t dims[5] = {16, nx, ny, zs, (cuuint64_t)(g.nz / g.zs)};
+    const cuuint64_t strides[4] = {row, row * nx, row * nx * ny, row * nx * ny * zs};
+    const cuuint32_t box[5] = {16, TC_HX, TC_HY, 1, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUtensorMap tm;
+    const CUresult r = encode(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)X, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(HEC_ERR_CUDA, "net: cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    const int xt = (g.nx + TCX - 1) / TCX, yt = (g.ny + TCY - 1) / TCY, zt = (g.zs + TCZ - 1) / TCZ;
+    const long items = (long)xt * yt * zt * (g.nz / g.zs);
+    if (items > (1L << 30)) return set_error(HEC_ERR_INVALID_ARG, "net: grid too large");
+    const int grid = (int)std::min<long>(items, 2L * std::max(1, num_sms()));
+    k_conv_tc<NT><<<grid, kTcThreads, TC_SMEM, s>>>(g, xt, yt, zt, (int)items, tm, W, bias, relu, out, status);
+    count_launch();
+    return HEC_OK;
+}
+
 // forward through all layers from `in` (N->act[0], or the solver's vectors); `last` receives
 // the last layer's output
 hec_status forward(hec_net* N, const Geom& g, const ConvIn& in, const ConvOut& last, cudaStream_t s) {
@@ -538,13 +876,20 @@ hec_status forward(hec_net* N, const Geom& g, const ConvIn& in, const ConvOut& l
     ConvOut o = none;
     o.Y = N->act[1];
     HEC_CHECK((conv<EXPAND, 2>(g, in, N->Wx, b[0], 1, o, s)));
+    const bool tc = N->tensor_cores != 0;
     for (int l = 1; l < NL - 1; ++l) {
         o.Y = N->act[l + 1];
-        HEC_CHECK((conv<PLAIN, 2>(g, ConvIn{N->act[l], nullptr, nullptr, nullptr, nullptr}, N->Wf + (long)l * WSZ, b[l], 1,
-                                  o, s)));
+        if (tc)
+            HEC_CHECK(conv_tc<2>(g, N->act[l], N->Wf + (long)l * WSZ, b[l], 1, o, N->status, s));
+        else
+            HEC_CHECK((conv<PLAIN, 2>(g, ConvIn{N->act[l], nullptr, nullptr, nullptr, nullptr}, N->Wf + (long)l * WSZ,
+                                      b[l], 1, o, s)));
     }
-    HEC_CHECK((conv<PLAIN, 1>(g, ConvIn{N->act[NL - 1], nullptr, nullptr, nullptr, nullptr},
-                              N->Wf + (long)(NL - 1) * WSZ, b[NL - 1], 0, last, s)));
+    if (tc)
+        HEC_CHECK(conv_tc<1>(g, N->act[NL - 1], N->Wf + (long)(NL - 1) * WSZ, b[NL - 1], 0, last, N->status, s));
+    else
+        HEC_CHECK((conv<PLAIN, 1>(g, ConvIn{N->act[NL - 1], nullptr, nullptr, nullptr, nullptr},
+                                  N->Wf + (long)(NL - 1) * WSZ, b[NL - 1], 0, last, s)));
     HEC_CUDA(cudaGetLastError());
     return HEC_OK;
 }
@@ -647,7 +992,7 @@ HEC_API hec_status net_create(const float* params, hec_net** out) {
     hec_status st = HEC_OK;
     if ((st = dalloc(&N->P, np)) || (st = dalloc(&N->G, np)) || (st = dalloc(&N->M, np)) || (st = dalloc(&N->V, np)) ||
         (st = dalloc(&N->Wf, (size_t)NL * WSZ)) || (st = dalloc(&N->Wd, (size_t)NL * WSZ)) ||
-        (st = dalloc(&N->Wx, (size_t)9 * C * C)) || (st = dalloc(&N->lpart, 4096))) {
+        (st = dalloc(&N->Wx, (size_t)9 * C * C)) || (st = dalloc(&N->lpart, 4096)) || (st = dalloc(&N->status, 1))) {
         free_net(N);
         return st;
     }
@@ -656,11 +1001,32 @@ HEC_API hec_status net_create(const float* params, hec_net** out) {
     cudaMemset(N->V, 0, sizeof(float) * np);
     cudaMemset(N->G, 0, sizeof(float) * np);
     cudaMemset(N->Wx, 0, sizeof(__nv_bfloat16) * 9 * C * C);
+    cudaMemset(N->status, 0, sizeof(int));
     st = refresh_weights(N, 0);
     if (st == HEC_OK && cudaDeviceSynchronize() != cudaSuccess) st = cuda_error(cudaGetLastError(), "net_create");
     if (st) { free_net(N); return st; }
     *out = N;
     return HEC_OK;
+}
+
+HEC_API hec_status net_set_engine(hec_net* N, int tensor_cores) {
+    clear_error();
+    if (!N) return set_error(HEC_ERR_INVALID_ARG, "net_set_engine: NULL");
+    N->tensor_cores = tensor_cores ? 1 : 0;
+    return HEC_OK;
+}
+
+HEC_API hec_status net_sync_status(hec_net* N, void* stream) {
+    clear_error();
+    if (!N) return set_error(HEC_ERR_INVALID_ARG, "net_sync_status: NULL");
+    cudaStream_t s = S(stream);
+    int h = 0;
+    HEC_CUDA(cudaMemcpyAsync(&h, N->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HEC_CUDA(cudaStreamSynchronize(s));
+    if (h == HEC_OK) return HEC_OK;
+    HEC_CUDA(cudaMemsetAsync(N->status, 0, sizeof(int), s));
+    HEC_CUDA(cudaStreamSynchronize(s));
+    return set_error((hec_status)h, "net: a tensor-core convolution's wait for its MMAs timed out");
 }
 
 HEC_API hec_status net_destroy(hec_net* N) {

@@ -781,7 +781,8 @@ HEC_API hec_status fgmres_solve(const hec_matrix* A, const ilu_precond* M, const
         if (!M) return HEC_OK;
         hec_status a = hec_sync_status(M->L, stream);
         hec_status c = hec_sync_status(M->U, stream);
-        return a != HEC_OK ? a : c;
+        hec_status d = extra ? net_sync_status(extra->net, stream) : HEC_OK;
+        return a != HEC_OK ? a : c != HEC_OK ? c : d;
     };
     while (true) {
         // r = b - A x; beta = ||r||; v_0 = r / beta (host decides on the restart)

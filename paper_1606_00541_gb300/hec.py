@@ -487,6 +487,8 @@ _net_train_step = _sig("net_train_step", _vp, _i, _i, _i, _i, _vp, _vp, ctypes.c
                        ctypes.POINTER(ctypes.c_float), _vp)
 _net_backward = _sig("net_backward", _vp, _i, _i, _i, _i, _vp, _vp, ctypes.POINTER(ctypes.c_float), _vp)
 _net_adam_step = _sig("net_adam_step", _vp, ctypes.c_float, _vp)
+_net_set_engine = _sig("net_set_engine", _vp, _i)
+_net_sync_status = _sig("net_sync_status", _vp, _vp)
 _stage_create = _sig("stage_create", _vp, _vp, _i, _i, _i, _vp, _d, _d, ctypes.POINTER(_vp))
 _stage_stats = _sig("stage_stats", _vp, ctypes.POINTER(_i), ctypes.POINTER(_i), _i)
 _stage_apply = _sig("stage_apply", _vp, _vp, _vp, _vp)
@@ -550,6 +552,14 @@ class Net(_Handle):
     def adam_step(self, lr=1e-3, stream=None):
         """One Adam step from the gradients of the last backward pass (net_adam_step)."""
         _check(_net_adam_step(self.h, float(lr), _stream(stream)), "net_adam_step")
+
+    def set_engine(self, tensor_cores=True):
+        """Forward layers 1-3 on tcgen05 (True, the default) or on mma.sync (net_set_engine)."""
+        _check(_net_set_engine(self.h, 1 if tensor_cores else 0), "net_set_engine")
+
+    def sync_status(self, stream=None):
+        """Raises HecError(TIMEOUT) when a tcgen05 convolution gave up waiting (net_sync_status)."""
+        _check(_net_sync_status(self.h, _stream(stream)), "net_sync_status")
 
 
 class Stage(_Handle):
