@@ -19,6 +19,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -330,11 +331,20 @@ __global__ void __launch_bounds__(kConvThreads, 4)
 // the loads and MMAs already issued are waited for (bounded) and the TMEM is freed.
 constexpr int TCX = 128, TCY = 2, TCZ = 8, TC_RING = 5;
 constexpr int TC_HX = TCX + 2, TC_HY = TCY + 2;
-constexpr int TC_SLAB = TC_HY * TC_HX * 32;               // one TMA box: 16,640 bytes (65 x 256)
 constexpr int TC_WBLK = 3 * C * C * 2;                     // B of one (dy, dx): 48 rows x 16 channels
-constexpr int TC_SMEM = TC_RING * TC_SLAB + 9 * TC_WBLK;   // 97,024 bytes: two CTAs per SM
 constexpr int TC_COLS = TCY * TCZ * 16;                    // 256 TMEM columns per CTA
-constexpr int kTcThreads = 192;
+// per variant (EXP = 0: 16 input channels, TMA slabs of 130 voxels per row; EXP = 1: the first
+// layer, slabs of 128 x-expanded voxels per row built by four producer warps)
+constexpr int tc_slab(int exp) { return TC_HY * (exp ? TCX : TC_HX) * 32; }  // 16,384 / 16,640 bytes
+constexpr int tc_sstr(int exp) { return (tc_slab(exp) + 1023) / 1024 * 1024; }  // 1024-byte aligned slabs
+constexpr int tc_nblk(int exp) { return exp ? 3 : 9; }                      // B blocks: dy, or (dy, dx)
+constexpr int TC_RAWR = 6, TC_RAWX = 132;                 // first layer: raw word rows, 6 planes deep
+constexpr int TC_RAWB = TC_HY * TC_RAWX * 4;               // one plane's raw rows: 2,112 bytes
+constexpr int tc_smem(int exp) {                           // 99,200 / 100,864 bytes
+    return TC_RING * tc_sstr(exp) + tc_nblk(exp) * TC_WBLK + (exp ? TC_RAWR * TC_RAWB : 0);
+}
+constexpr int tc_pwarps(int exp) { return exp ? 4 : 1; }                    // producer warps
+constexpr int tc_threads(int exp) { return 32 * (5 + tc_pwarps(exp)); }     // + 4 epilogue warps + 1 MMA warp
 constexpr long long kTcWaitBudget = 2000000000LL;          // clock cycles (about 1 s)
 
 // shared-memory matrix descriptors (version 1, base offset 0).  tc_desc: K-major, no swizzle,
@@ -382,22 +392,26 @@ __device__ __forceinline__ void tc_commit(unsigned mb) {
 struct TcItem {
     int x0, y0, z0, zc, sample;
 };
-__device__ __forceinline__ TcItem tc_item(int i, int xt, int yt, int zt, int zs) {
+// item i: x tile fastest, then y strip, z chunk (zl planes, zl <= TCZ) and sample
+__device__ __forceinline__ TcItem tc_item(int i, int xt, int yt, int zt, int zl, int zs) {
     TcItem t;
     t.x0 = (i % xt) * TCX;
     i /= xt;
     t.y0 = (i % yt) * TCY;
     i /= yt;
-    t.z0 = (i % zt) * TCZ;
+    t.z0 = (i % zt) * zl;
     t.sample = i / zt;
-    t.zc = min(TCZ, zs - t.z0);
+    t.zc = min(zl, zs - t.z0);
     return t;
 }
 
-template <int NT>
-__global__ void __launch_bounds__(kTcThreads, 2)
-    k_conv_tc(Geom g, int xt, int yt, int zt, int nitems, const __grid_constant__ CUtensorMap tmap,
+template <int NT, int EXP>
+__global__ void __launch_bounds__(tc_threads(EXP), 2)
+    k_conv_tc(Geom g, int xt, int yt, int zt, int zl, int nitems, const __grid_constant__ CUtensorMap tmap, ConvIn in,
+              int wstride,
               const __nv_bfloat16* __restrict__ W, const float* __restrict__ bias, int relu, ConvOut out, int* status) {
+    constexpr int SSTR = tc_sstr(EXP), NBLK = tc_nblk(EXP), NTHR = tc_threads(EXP), PW = tc_pwarps(EXP);
+    constexpr int MMA_WARP = 4 + PW;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) unsigned long long bar_full[TC_RING], bar_free[TC_RING], bar_done[TCZ], bar_drained[TCZ],
         bar_fin;
@@ -406,19 +420,20 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     volatile int* abort = &abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned sh = (unsigned)__cvta_generic_to_shared(smem);
-    const unsigned sw = sh + TC_RING * TC_SLAB;
+    const unsigned sw = sh + TC_RING * SSTR;
     auto bar = [](unsigned long long* b) { return (unsigned)__cvta_generic_to_shared(b); };
 
-    // B blocks: tap (dy, dx) = j, row n = dz*16 + co, half h -> sw + j*1536 + h*768 + n*16
-    for (int i = tid; i < 9 * 48 * 2; i += kTcThreads) {
+    // B blocks: j = (dy, dx) (dy for EXP), row n = dz*16 + co, half h -> sw + j*1536 + h*768 + n*16.
+    // W is [27 taps][co][ci], or for EXP [9 (dz, dy)][co][slot = 2 dx + ci]
+    for (int i = tid; i < NBLK * 48 * 2; i += NTHR) {
         const int h = i & 1, n = (i >> 1) % 48, j = (i >> 1) / 48;
-        const int tap = (n >> 4) * 9 + j, co = n & 15;
+        const int tap = (n >> 4) * NBLK + j, co = n & 15;
         cp_async16(sw + j * TC_WBLK + h * (TC_WBLK / 2) + n * 16, W + ((long)tap * C + co) * C + h * 8, 16);
     }
     if (tid == 0) {
         abort_flag = 0;
         for (int s = 0; s < TC_RING; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(&bar_full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(&bar_full[s])), "n"(EXP ? 32 * PW : 1));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(&bar_free[s])));
         }
         for (int k = 0; k < TCZ; ++k) {
@@ -428,7 +443,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(&bar_fin)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 5) {
+    if (warp == MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(&tmem_slot)),
                      "n"(TC_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -451,30 +466,108 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    if (warp == 4) {
-        // ---- TMA producer ----
-        if (lane == 0) {
-            int it = 0;
-            const unsigned long long tm = reinterpret_cast<unsigned long long>(&tmap);
-            for (int i = blockIdx.x; i < nitems && !*abort; i += gridDim.x) {
-                const TcItem t = tc_item(i, xt, yt, zt, g.zs);
-                for (int p = 0; p <= t.zc + 1; ++p, ++it) {
-                    const int s = it % TC_RING, use = it / TC_RING;
-                    if (use > 0 && !mbar_wait(bar(&bar_free[s]), (use - 1) & 1, abort)) break;
-                    const unsigned fb = bar(&bar_full[s]);
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "n"(TC_SLAB) : "memory");
-                    asm volatile(
-                        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-                        "%4, %5, %6}], [%7];" ::"r"(sh + s * TC_SLAB), "l"(tm), "r"(0), "r"(t.x0 - 1), "r"(t.y0 - 1),
-                        "r"(t.z0 - 1 + p), "r"(t.sample), "r"(fb)
-                        : "memory");
+    if (warp >= 4 && warp < 4 + PW) {
+        if constexpr (EXP == 0) {
+            // ---- TMA producer ----
+            if (lane == 0) {
+                int it = 0;
+                const unsigned long long tm = reinterpret_cast<unsigned long long>(&tmap);
+                for (int i = blockIdx.x; i < nitems && !*abort; i += gridDim.x) {
+                    const TcItem t = tc_item(i, xt, yt, zt, zl, g.zs);
+                    for (int p = 0; p <= t.zc + 1; ++p, ++it) {
+                        const int s = it % TC_RING, use = it / TC_RING;
+                        if (use > 0 && !mbar_wait(bar(&bar_free[s]), (use - 1) & 1, abort)) break;
+                        const unsigned fb = bar(&bar_full[s]);
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "n"(tc_slab(0))
+                                     : "memory");
+                        asm volatile(
+                            "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                            "%3, %4, %5, %6}], [%7];" ::"r"(sh + s * SSTR), "l"(tm), "r"(0), "r"(t.x0 - 1), "r"(t.y0 - 1),
+                            "r"(t.z0 - 1 + p), "r"(t.sample), "r"(fb)
+                            : "memory");
+                    }
+                    if (*abort) break;
                 }
-                if (*abort) break;
+                // the loads already issued land before the CTA ends (each slab's last fill)
+                for (int k = it - 1; k >= 0 && k >= it - TC_RING; --k)
+                    mbar_drain(bar(&bar_full[k % TC_RING]), (k / TC_RING) & 1);
             }
-            // the loads already issued land before the CTA ends (each slab's last fill)
-            for (int k = it - 1; k >= 0 && k >= it - TC_RING; --k) mbar_drain(bar(&bar_full[k % TC_RING]), (k / TC_RING) & 1);
+        } else {
+            // ---- first layer: four warps build the x-expanded slab.  The source is one 32-bit word per
+            // voxel holding channels 0-1 (in.X with a stride of wstride words).  Its rows x0-1 ..
+            // x0+128 of the next TC_RAWR-1 planes are in flight in a ring of raw rows (cp.async, zeros
+            // outside the grid or the sample); row e = hr * 128 + m of the slab then gets, for voxel
+            // x0 + m of halo row hr, the words of x-1, x, x+1 in slots 0-5, in the 32-byte swizzle the
+            // MMAs read.  The four warps step together (named barrier 1); a stop decided by thread 0
+            // from the abort flag is read by all of them after the barrier.
+            __shared__ int prod_stop[2];
+            const int m = tid - 128;
+            const unsigned raw = sw + NBLK * TC_WBLK;
+            const unsigned* __restrict__ src = (const unsigned*)in.X;
+            int fi = blockIdx.x, fp = 0, nf = 0;  // fetch cursor: item, plane, planes fetched
+            TcItem ft{};
+            if (fi < nitems) ft = tc_item(fi, xt, yt, zt, zl, g.zs);
+            auto fetch = [&]() {
+                if (fi < nitems) {
+                    const unsigned base = raw + (nf % TC_RAWR) * TC_RAWB;
+                    const long sbase = (long)ft.sample * g.zs;
+                    const int z = ft.z0 - 1 + fp;
+                    for (int e = m; e < TC_HY * (TCX + 2); e += 32 * PW) {
+                        const int hr = e / (TCX + 2), j = e % (TCX + 2), x = ft.x0 - 1 + j, y = ft.y0 - 1 + hr;
+                        const bool inb = x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.zs;
+                        const unsigned* a = inb ? src + (((sbase + z) * g.ny + y) * g.nx + x) * wstride : src;
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(base + (hr * TC_RAWX + j) * 4),
+                                     "l"(a), "r"(inb ? 4 : 0)
+                                     : "memory");
+                    }
+                    ++nf;
+                    if (++fp > ft.zc + 1) {
+                        fp = 0;
+                        fi += gridDim.x;
+                        if (fi < nitems) ft = tc_item(fi, xt, yt, zt, zl, g.zs);
+                    }
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");  // one group per call, empty or not
+            };
+            for (int k = 0; k < TC_RAWR - 1; ++k) fetch();
+            int i = blockIdx.x, p = 0, q = 0;  // convert cursor: item, plane, planes converted
+            TcItem t{};
+            if (i < nitems) t = tc_item(i, xt, yt, zt, zl, g.zs);
+            while (i < nitems) {
+                if (m == 0) prod_stop[q & 1] = *abort;
+                asm volatile("bar.sync 1, %0;" ::"n"(32 * PW) : "memory");  // plane q-1's raw rows are free
+                if (prod_stop[q & 1]) break;
+                fetch();                                                     // plane q + TC_RAWR - 1
+                asm volatile("cp.async.wait_group %0;" ::"n"(TC_RAWR - 1) : "memory");
+                asm volatile("bar.sync 1, %0;" ::"n"(32 * PW) : "memory");  // plane q's raw rows landed
+                const int s = q % TC_RING, use = q / TC_RING;
+                if (use > 0) mbar_wait(bar(&bar_free[s]), (use - 1) & 1, abort);  // a timeout stops us next plane
+                const unsigned rb = raw + (q % TC_RAWR) * TC_RAWB;
+#pragma unroll
+                for (int hr = 0; hr < TC_HY; ++hr) {
+                    unsigned w0, w1, w2;
+                    const unsigned ra = rb + (hr * TC_RAWX + m) * 4;
+                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w0) : "r"(ra));
+                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w1) : "r"(ra + 4));
+                    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w2) : "r"(ra + 8));
+                    const int e = hr * TCX + m;
+                    const unsigned sa = sh + s * SSTR + e * 32, sw_bit = ((unsigned)e >> 2) & 1u;
+                    asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(sa + (sw_bit << 4)), "r"(w0), "r"(w1),
+                                 "r"(w2), "r"(0u));
+                    asm volatile("st.shared.v4.u32 [%0], {%1,%1,%1,%1};" ::"r"(sa + ((sw_bit ^ 1u) << 4)), "r"(0u));
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(&bar_full[s])) : "memory");
+                ++q;
+                if (++p > t.zc + 1) {
+                    p = 0;
+                    i += gridDim.x;
+                    if (i < nitems) t = tc_item(i, xt, yt, zt, zl, g.zs);
+                }
+            }
+            asm volatile("cp.async.wait_all;" ::: "memory");  // no copy lands after the CTA ends
         }
-    } else if (warp == 5) {
+    } else if (warp == MMA_WARP) {
         // ---- MMA issuer ----
         if (lane == 0) {
             const unsigned base_idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TCX >> 4) << 24);
@@ -482,7 +575,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
             int it = 0;
             bool issued = false;
             for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
-                const TcItem t = tc_item(i, xt, yt, zt, g.zs);
+                const TcItem t = tc_item(i, xt, yt, zt, zl, g.zs);
                 bool ok = true;
                 for (int p = 0; p <= t.zc + 1 && ok; ++p, ++it) {
                     const int s = it % TC_RING;
@@ -496,16 +589,18 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                     const int nn = (dz_hi - dz_lo + 1) * 16;
                     const unsigned idesc = base_idesc | ((unsigned)(nn >> 3) << 17);
                     const int kcol = (TCZ - 1 - (p - dz_lo)) * 16;  // first column: plane p - dz_lo
-                    const unsigned slab = sh + s * TC_SLAB;
+                    const unsigned slab = sh + s * SSTR;
 #pragma unroll
                     for (int y = 0; y < TCY; ++y)
 #pragma unroll
                         for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-                            for (int dx = 0; dx < 3; ++dx) {
-                                const unsigned long long ad = tc_desc_sw32(slab + ((y + dy) * TC_HX + dx) * 32);
+                            for (int dx = 0; dx < 3 - 2 * EXP; ++dx) {
+                                // EXP: the three dx taps are in K; the A row of voxel x0 + m is row m
+                                const unsigned long long ad =
+                                    tc_desc_sw32(slab + (EXP ? (y + dy) * TCX : (y + dy) * TC_HX + dx) * 32);
                                 const unsigned long long bd =
-                                    tc_desc(sw + (dy * 3 + dx) * TC_WBLK + dz_lo * 256, TC_WBLK / 2);
+                                    tc_desc(sw + (EXP ? dy : dy * 3 + dx) * TC_WBLK + dz_lo * 256, TC_WBLK / 2);
                                 asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, 1, 0;\n"
                                              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
                                              ::"r"(tmem + y * (TCZ * 16) + kcol), "l"(ad), "l"(bd), "r"(idesc));
@@ -531,7 +626,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         const unsigned lane_base = tmem + ((unsigned)(warp * 32) << 16);
         bool ok = true;
         for (int i = blockIdx.x; i < nitems && ok; i += gridDim.x) {
-            const TcItem t = tc_item(i, xt, yt, zt, g.zs);
+            const TcItem t = tc_item(i, xt, yt, zt, zl, g.zs);
             const int x = t.x0 + warp * 32 + lane;
             for (int k = 0; k < t.zc; ++k) {
                 ok = __all_sync(0xffffffffu, mbar_wait(bar(&bar_done[k]), (dpar >> k) & 1u, abort));
@@ -590,7 +685,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 5) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TC_COLS));
+    if (warp == MMA_WARP) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TC_COLS));
 }
 
 // Weight and bias gradients of one layer: partial[block][tap][ci][co] = sum over this tile's voxels
@@ -750,7 +845,8 @@ struct hec_net {
     float* partial = nullptr;
     long partial_cap = 0;
     float* lpart = nullptr;
-    int tensor_cores = 1;              // forward 16-channel layers on tcgen05 (else mma.sync)
+    int tensor_cores = 1;              // forward pass on tcgen05 (else mma.sync)
+    unsigned* words = nullptr;         // [cap] first-layer input: BF16 channels 0-1 of each voxel
     int* status = nullptr;             // device word: HEC_ERR_TIMEOUT if a tensor-core wait ran out
 };
 
@@ -762,7 +858,7 @@ void free_net(hec_net* N) {
     cudaFree(N->P); cudaFree(N->G); cudaFree(N->M); cudaFree(N->V); cudaFree(N->Wf); cudaFree(N->Wd); cudaFree(N->Wx);
     for (auto& a : N->act) cudaFree(a);
     for (auto& a : N->dA) cudaFree(a);
-    cudaFree(N->out); cudaFree(N->partial); cudaFree(N->lpart); cudaFree(N->status);
+    cudaFree(N->out); cudaFree(N->partial); cudaFree(N->lpart); cudaFree(N->status); cudaFree(N->words);
     delete N;
 }
 
@@ -771,11 +867,14 @@ hec_status ensure(hec_net* N, long nvox, long nblk) {
         for (auto& a : N->act) { cudaFree(a); a = nullptr; }
         for (auto& a : N->dA) { cudaFree(a); a = nullptr; }
         cudaFree(N->out);
+        cudaFree(N->words);
         N->out = nullptr;
+        N->words = nullptr;
         N->cap = 0;
         for (auto& a : N->act) HEC_CHECK(dalloc(&a, (size_t)nvox * C));
         for (auto& a : N->dA) HEC_CHECK(dalloc(&a, (size_t)nvox * C));
         HEC_CHECK(dalloc(&N->out, (size_t)nvox));
+        HEC_CHECK(dalloc(&N->words, (size_t)nvox));
         N->cap = nvox;
     }
     if (nblk > N->partial_cap) {
@@ -822,6 +921,15 @@ hec_status conv(const Geom& g, const ConvIn& in, const __nv_bfloat16* W, const f
     return HEC_OK;
 }
 
+// first-layer input from the solver's vectors: word v = (BF16(r[v] / sigma), aux[v]), channel 0 = 0
+// when sigma is not positive (as the mma.sync path stages it)
+__global__ void k_words(long n, const double* __restrict__ r, const double* __restrict__ sigma,
+                        const __nv_bfloat16* __restrict__ aux, unsigned* __restrict__ w) {
+    const double inv = *sigma > 0.0 ? 1.0 / *sigma : 0.0;
+    for (long v = (long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long)gridDim.x * blockDim.x)
+        w[v] = pack2(__float2bfloat16_rn((float)(r[v] * inv)), aux[v]);
+}
+
 // the 16-input-channel forward convolution on the tensor cores (see k_conv_tc)
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -835,33 +943,48 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-template <int NT>
-hec_status conv_tc(const Geom& g, const __nv_bfloat16* X, const __nv_bfloat16* W, const float* bias, int relu,
-                   const ConvOut& out, int* status, cudaStream_t s) {
+template <int NT, int EXP>
+hec_status conv_tc(const Geom& g, const ConvIn& in, const __nv_bfloat16* W, const float* bias, int relu,
+                   const ConvOut& out, int* status, cudaStream_t s, int wstride = 0) {
     static bool smem_set = false;
     if (!smem_set) {
-        HEC_CUDA(cudaFuncSetAttribute(k_conv_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+        HEC_CUDA(cudaFuncSetAttribute(k_conv_tc<NT, EXP>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(EXP)));
         smem_set = true;
     }
-    auto encode = tensor_map_encoder();
-    if (!encode) return set_error(HEC_ERR_CUDA, "net: cuTensorMapEncodeTiled is not available");
-    // X viewed as [sample][z][y][x][16 channels]; a box is 130 voxels x (TCY+2) rows of one plane,
-    // written to shared memory in the 32-byte swizzle
-    const cuuint64_t row = 32, nx = (cuuint64_t)g.nx, ny = (cuuint64_t)g.ny, zs = (cuuint64_t)g.zs;
-    const cuuint64_t dims[5] = {16, nx, ny, zs, (cuuint64_t)(g.nz / g.zs)};
-    const cuuint64_t strides[4] = {row, row * nx, row * nx * ny, row * nx * ny * zs};
-    const cuuint32_t box[5] = {16, TC_HX, TC_HY, 1, 1};
-    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     CUtensorMap tm;
-    const CUresult r = encode(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)X, dims, strides, box, estr,
-                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return set_error(HEC_ERR_CUDA, "net: cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
-    const int xt = (g.nx + TCX - 1) / TCX, yt = (g.ny + TCY - 1) / TCY, zt = (g.zs + TCZ - 1) / TCZ;
-    const long items = (long)xt * yt * zt * (g.nz / g.zs);
+    memset(&tm, 0, sizeof(tm));
+    if (!EXP) {
+        auto encode = tensor_map_encoder();
+        if (!encode) return set_error(HEC_ERR_CUDA, "net: cuTensorMapEncodeTiled is not available");
+        // X viewed as [sample][z][y][x][16 channels]; a box is 130 voxels x (TCY+2) rows of one
+        // plane, written to shared memory in the 32-byte swizzle
+        const cuuint64_t row = 32, nx = (cuuint64_t)g.nx, ny = (cuuint64_t)g.ny, zs = (cuuint64_t)g.zs;
+        const cuuint64_t dims[5] = {16, nx, ny, zs, (cuuint64_t)(g.nz / g.zs)};
+        const cuuint64_t strides[4] = {row, row * nx, row * nx * ny, row * nx * ny * zs};
+        const cuuint32_t box[5] = {16, TC_HX, TC_HY, 1, 1};
+        const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+        const CUresult r = encode(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)in.X, dims, strides, box, estr,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return set_error(HEC_ERR_CUDA, "net: cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    }
+    const int xt = (g.nx + TCX - 1) / TCX, yt = (g.ny + TCY - 1) / TCY, ns = g.nz / g.zs;
+    const long G = 2L * std::max(1, num_sms());  // two CTAs per SM, persistent
+    // z-chunk length: the one that minimises the busiest CTA's plane steps, ceil(items / G) x (zl + 2)
+    int zl = TCZ;
+    long best = -1;
+    for (int L = TCZ; L >= 1; --L) {
+        const long zt = (g.zs + L - 1) / L, items = (long)xt * yt * zt * ns;
+        const long cost = (items + G - 1) / G * (L + 2);
+        if (best < 0 || cost < best) best = cost, zl = L;
+    }
+    const int zt = (g.zs + zl - 1) / zl;
+    const long items = (long)xt * yt * zt * ns;
     if (items > (1L << 30)) return set_error(HEC_ERR_INVALID_ARG, "net: grid too large");
-    const int grid = (int)std::min<long>(items, 2L * std::max(1, num_sms()));
-    k_conv_tc<NT><<<grid, kTcThreads, TC_SMEM, s>>>(g, xt, yt, zt, (int)items, tm, W, bias, relu, out, status);
+    const int grid = (int)std::min<long>(items, G);
+    k_conv_tc<NT, EXP><<<grid, tc_threads(EXP), tc_smem(EXP), s>>>(g, xt, yt, zt, zl, (int)items, tm, in, wstride, W,
+                                                                  bias, relu, out, status);
     count_launch();
     return HEC_OK;
 }
@@ -875,18 +998,31 @@ hec_status forward(hec_net* N, const Geom& g, const ConvIn& in, const ConvOut& l
     const ConvOut none{nullptr, nullptr, 1.f, nullptr, nullptr};
     ConvOut o = none;
     o.Y = N->act[1];
-    HEC_CHECK((conv<EXPAND, 2>(g, in, N->Wx, b[0], 1, o, s)));
     const bool tc = N->tensor_cores != 0;
+    if (tc && in.r) {
+        // the solver's vectors: channels 0-1 packed into one word per voxel first
+        const long nvox = (long)g.nx * g.ny * g.nz;
+        k_words<<<(int)std::min<long>((nvox + 255) / 256, 8L * std::max(1, num_sms())), 256, 0, s>>>(nvox, in.r, in.sigma,
+                                                                                                   in.aux, N->words);
+        count_launch();
+        HEC_CHECK((conv_tc<2, 1>(g, ConvIn{(const __nv_bfloat16*)N->words, nullptr, nullptr, nullptr, nullptr}, N->Wx,
+                                 b[0], 1, o, N->status, s, 1)));
+    } else if (tc) {
+        HEC_CHECK((conv_tc<2, 1>(g, in, N->Wx, b[0], 1, o, N->status, s, C / 2)));  // word 0 of each 16-channel voxel
+    } else
+        HEC_CHECK((conv<EXPAND, 2>(g, in, N->Wx, b[0], 1, o, s)));
     for (int l = 1; l < NL - 1; ++l) {
         o.Y = N->act[l + 1];
         if (tc)
-            HEC_CHECK(conv_tc<2>(g, N->act[l], N->Wf + (long)l * WSZ, b[l], 1, o, N->status, s));
+            HEC_CHECK((conv_tc<2, 0>(g, ConvIn{N->act[l], nullptr, nullptr, nullptr, nullptr}, N->Wf + (long)l * WSZ, b[l],
+                                     1, o, N->status, s)));
         else
             HEC_CHECK((conv<PLAIN, 2>(g, ConvIn{N->act[l], nullptr, nullptr, nullptr, nullptr}, N->Wf + (long)l * WSZ,
                                       b[l], 1, o, s)));
     }
     if (tc)
-        HEC_CHECK(conv_tc<1>(g, N->act[NL - 1], N->Wf + (long)(NL - 1) * WSZ, b[NL - 1], 0, last, N->status, s));
+        HEC_CHECK((conv_tc<1, 0>(g, ConvIn{N->act[NL - 1], nullptr, nullptr, nullptr, nullptr},
+                                 N->Wf + (long)(NL - 1) * WSZ, b[NL - 1], 0, last, N->status, s)));
     else
         HEC_CHECK((conv<PLAIN, 1>(g, ConvIn{N->act[NL - 1], nullptr, nullptr, nullptr, nullptr},
                                   N->Wf + (long)(NL - 1) * WSZ, b[NL - 1], 0, last, s)));

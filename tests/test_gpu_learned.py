@@ -89,9 +89,9 @@ def test_forward_layer_parity(hec, dims, zs, tensor_cores):
 
 def test_engines_agree(hec):
     """The tcgen05 and mma.sync forward passes add the same BF16 products in FP32 in a different
-    order.  Layer 1 (same input in both) differs by at most one BF16 unit in the last place, where
-    the two sums straddle a rounding boundary; the layers after it see inputs that differ in those
-    places, so they and the output are compared in norm."""
+    order.  The first layer (same input in both) differs by at most one BF16 unit in the last place,
+    where the two sums straddle a rounding boundary; the layers after it see inputs that differ in
+    those places, so they and the output are compared in norm."""
     from paper_1606_00541_gb300 import learn
     rng = np.random.default_rng(4)
     dims, zs = (200, 20, 24), 24
@@ -104,11 +104,10 @@ def test_engines_agree(hec):
         net.sync_status()
         res.append((out.cpu().numpy().astype(np.float64), acts.float().cpu().numpy().astype(np.float64)))
     (o1, a1), (o0, a0) = res
-    assert np.array_equal(a1[0], a0[0])  # layer 0 runs the same kernel in both
-    d = np.abs(a1[1] - a0[1])
-    assert np.all(d <= 2.0 ** -7 * np.maximum(np.abs(a1[1]), np.abs(a0[1])) + 1e-6)
+    d = np.abs(a1[0] - a0[0])
+    assert np.all(d <= 2.0 ** -7 * np.maximum(np.abs(a1[0]), np.abs(a0[0])) + 1e-6)
     assert np.mean(d > 0) < 0.05
-    for li in (2, 3):
+    for li in (1, 2, 3):
         assert np.linalg.norm(a1[li] - a0[li]) <= 2.0 ** -8 * np.linalg.norm(a0[li]), li
     assert np.linalg.norm(o1 - o0) <= 2.0 ** -8 * np.linalg.norm(o0)
 
