@@ -350,10 +350,9 @@ hec_status net_train_step(hec_net* net, int nx, int ny, int nz, int zs, const vo
 hec_status net_backward(hec_net* net, int nx, int ny, int nz, int zs, const void* x_in,
                         const float* target, float* loss_out, void* stream);
 hec_status net_adam_step(hec_net* net, float lr, void* stream);
-/* The forward pass computes the layers with 16 input channels (layers 1-3) with tcgen05 MMAs
- * (tensor_cores = 1, the default) or with the warp-level mma.sync path (0); both accumulate the
- * same BF16 products in FP32, in a different order.  Layer 0 and the backward pass always use
- * mma.sync. */
+/* The forward pass (all four layers) runs on tcgen05 MMAs (tensor_cores = 1, the default) or on
+ * the warp-level mma.sync path (0); both accumulate the same BF16 products in FP32, in a different
+ * order.  The backward pass (net_backward, net_train_step) always uses mma.sync. */
 hec_status net_set_engine(hec_net* net, int tensor_cores);
 /* Synchronizes `stream` and returns HEC_ERR_TIMEOUT (then clears it) when a tcgen05 convolution
  * since the last call gave up waiting for its MMAs (its outputs were not written), else HEC_OK.

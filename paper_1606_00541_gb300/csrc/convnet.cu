@@ -8,10 +8,12 @@
 // z (zs planes each); the convolution treats the sample boundaries as zero padding.
 //
 // Convolution = implicit GEMM: for each of the 27 taps, D[voxels x 16 out] += X_shifted[voxels x
-// 16 in] * W_tap[16 in x 16 out], one mma.sync.m16n8k16 (BF16 in, FP32 accumulate) per 16
-// voxels per 8 output channels per tap.  A forward block computes a 32 x 4 x 4 voxel tile from a
-// 34 x 6 x 6 halo tile staged in shared memory together with all 27 weight taps (the weight-gradient
-// kernel works on 32 x 4 x 1 tiles with a 34 x 6 x 3 halo).  The data gradient is the
+// 16 in] * W_tap[16 in x 16 out].  The forward pass runs on tcgen05 (k_conv_tc: TMA-fed slabs,
+// TMEM accumulators; see there).  The mma.sync path (one m16n8k16, BF16 in, FP32 accumulate, per
+// 16 voxels per 8 output channels per tap) serves the backward pass and the forward pass when the
+// tensor-core engine is switched off (net_set_engine).  A k_conv forward block computes a
+// 32 x 4 x 4 voxel tile from a 34 x 6 x 6 halo tile staged in shared memory together with all 27
+// weight taps (the weight-gradient kernel works on 32 x 4 x 1 tiles with a 34 x 6 x 3 halo).  The data gradient is the
 // same kernel run with the spatially flipped, channel-transposed weights and the ReLU mask of
 // the layer applied while the halo is staged; the weight gradient is a GEMM over voxels with
 // per-block partial sums reduced in a fixed order (deterministic).
