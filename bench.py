@@ -248,9 +248,10 @@ def main():
                     help="at most this many timed oracle steps (each a whole solve) in the reference arm")
     ap.add_argument("--sweep", default="part", choices=["part", "global"],
                     help="single-RHS sweep schedule of the timed step: x-pencil partitioned (default) or global")
-    ap.add_argument("--apply-only", choices=["ilu0_16rhs", "ras64_16rhs"], default=None,
-                    help="only time the 16-right-hand-side L+U apply of this preconditioner (a short run, e.g. "
-                         "to profile the multi-right-hand-side sweep)")
+    ap.add_argument("--apply-only", choices=["ilu0_16rhs", "ras64_16rhs", "stage"], default=None,
+                    help="only time the 16-right-hand-side L+U apply of this preconditioner, or one learned-stage "
+                         "application (a short run, e.g. to profile the multi-right-hand-side sweep or the "
+                         "convolution)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -709,12 +710,50 @@ def long_row_variant(hec, torch, hbm, device, m=100, ilut=None):
     return out
 
 
+def run_stage_only(args):
+    """One learned-stage application (z1 -> z: the residual's SpMV, the 4-layer network on the m^3
+    field, the correction's SpMV and the gated step) on the log-normal 7-point problem with ILU(0)
+    FP32 factors and an untrained network, W untimed and K timed applications per engine (tcgen05,
+    then mma.sync); prints one JSON line with the application times."""
+    import torch
+    from paper_1606_00541_gb300 import hec, learn, synth
+    m = args.size
+    n = m ** 3
+    lnk = np.log(synth.lognormal_perm(m, 2.0, 0))
+    A = synth.fv7_lognormal(m, perm=np.exp(lnk))
+    Ad = [torch.as_tensor(a, device="cuda") for a in A]
+    Lh, Uh = hec.ilu_factor(*Ad, k=0)
+    s = hec.IluSolver(Lh.tensors(), Uh.tensors(), A=Ad, vdt="f32")
+    net = hec.Net(learn.init_params(1))
+    stage = hec.Stage(net, s.A, (m, m, m), torch.as_tensor(lnk, device="cuda"))
+    v = torch.as_tensor(synth.uniform_vector(n, 7), device="cuda")
+    z1 = s.apply(v)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"apply": "stage", "n": n}
+    for engine, tc in (("tcgen05", True), ("mma_sync", False)):
+        net.set_engine(tc)
+        for _ in range(args.warmup):
+            stage.apply(v, z1)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            stage.apply(v, z1)
+        e1.record()
+        torch.cuda.synchronize()
+        net.sync_status()
+        out["stage_apply_us_" + engine] = e0.elapsed_time(e1) * 1000.0 / args.steps
+    net.set_engine(True)
+    print(json.dumps(out), flush=True)
+
+
 def run_apply_only(args):
     """The 16-right-hand-side L+U apply of one preconditioner (GPU ILU(0) of the whole matrix, or
     RAS with 64 box subdomains), FP32 factor values, autotuned launch shape: W untimed and K timed
     applies; prints one JSON line with the apply time and its algorithmic GB/s."""
     import torch
     from paper_1606_00541_gb300 import hec, synth
+    if args.apply_only == "stage":
+        return run_stage_only(args)
     m = args.size
     n = m ** 3
     A, _ = make_problem(m)
