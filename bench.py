@@ -412,6 +412,7 @@ def main():
                     head["latency_floor_us"] = roofline["latency_floor"]["floor_us"]
                     head["sweep_us"] = roofline["avg_sweep_us"]
                 head["breakdown_ms"] = line.get("breakdown_ms")
+                head["gram_schmidt"] = gram_schmidt_times(hec, torch, Ad, L, U, bd, sched)
         line = head
     if rank == 0 and not args.no_variants:
         line["variants"] = variants(hec, torch, Ad, L, U, bd, HA0, n, nnzL, nnzU, hbm, Schedule("part", m, devn, torch))
@@ -452,7 +453,39 @@ def precision_times(hec, torch, Ad, L, U, bd, sched):
         e1.record()
         torch.cuda.synchronize()
         out[vdt] = {"time_to_1e-8_s": e0.elapsed_time(e1) / 1000.0, "iterations": info["iterations"],
-                    "converged": info["converged"]}
+                    "converged": info["converged"], "reorthogonalized": info["reorthogonalized"]}
+    return out
+
+
+def gram_schmidt_times(hec, torch, Ad, L, U, bd, sched):
+    """Time to 1e-8 with FP32 factor values under each Gram-Schmidt variant of the Arnoldi step
+    (classical with selective reorthogonalization, the library default, and modified), and the
+    device time of the Gram-Schmidt kernel in each solve."""
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    default = hec.get_gram_schmidt()
+    try:
+        for mode in ("classical", "modified"):
+            hec.set_gram_schmidt(mode)
+            s = hec.IluSolver(L, U, A=Ad, vdt="f32")
+            sched.apply(s, "f32")
+            s.solve(bd, restart=RESTART, rtol=RTOL, max_iters=5000)
+            torch.cuda.synchronize()
+            e0.record()
+            _, info = s.solve(bd, restart=RESTART, rtol=RTOL, max_iters=5000)
+            e1.record()
+            torch.cuda.synchronize()
+            hec.profile_enable(True, categories=[2])
+            hec.profile_read(reset=True)
+            s.solve(bd, restart=RESTART, rtol=RTOL, max_iters=5000)
+            torch.cuda.synchronize()
+            gs_ms = hec.profile_breakdown()["gram_schmidt"][0]
+            hec.profile_read(reset=True)
+            hec.profile_enable(False)
+            out[mode] = {"time_to_1e-8_s": e0.elapsed_time(e1) / 1000.0, "iterations": info["iterations"],
+                         "reorthogonalized": info["reorthogonalized"], "gram_schmidt_ms": round(gs_ms, 3)}
+    finally:
+        hec.set_gram_schmidt(default)
     return out
 
 

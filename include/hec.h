@@ -282,12 +282,29 @@ typedef struct {
     int converged;       /* 1 when every right-hand side reached rtol */
     double rel_residual; /* largest true relative residual ||b - A x|| / ||b|| at exit */
     double seconds;      /* wall time of the call, host clock */
+    int reorthogonalized; /* inner iterations that took a second Gram-Schmidt pass (classical mode) */
 } hec_fgmres_info;
 
+/* Gram-Schmidt variant of the Arnoldi step in fgmres_solve, process-wide (default
+ * HEC_GS_CLASSICAL).  Both are FP64 and equal in exact arithmetic; the paper runs GMRES without
+ * naming one (Sec. 4).
+ *   HEC_GS_CLASSICAL: all inner products h = V^T w from the same w (one grid-wide reduction a
+ *     step), w -= V h, and a second pass (h2 = V^T w, w -= V h2) for a right-hand side whose norm
+ *     fell below 0.25 ||w|| (selective reorthogonalization); ||w - V h|| from ||w||^2 - ||h||^2
+ *     when no second pass runs.  hec_fgmres_info.reorthogonalized counts the second passes.
+ *   HEC_GS_MODIFIED: one projection at a time (one grid-wide reduction per projection), as the
+ *     textbook modified Gram-Schmidt.
+ * Returns HEC_ERR_INVALID_ARG for any other value.  Not thread-safe against a concurrent
+ * fgmres_solve call (the mode is read once when a solve starts). */
+enum { HEC_GS_CLASSICAL = 0, HEC_GS_MODIFIED = 1 };
+hec_status hec_set_gram_schmidt(int mode);
+int hec_get_gram_schmidt(void);
+
 /* Solves A x = b by right-preconditioned flexible GMRES(restart), z_j = M^-1 v_j with the ILU
- * or RAS preconditioner M (NULL = none), FP64 throughout: SpMV, modified Gram-Schmidt (one
- * persistent kernel per inner iteration, a fixed-order grid-wide reduction per projection),
- * Givens rotations.  Each of the nrhs right-hand sides (row-major n x nrhs, nrhs <= 16) has its
+ * or RAS preconditioner M (NULL = none), FP64 throughout: SpMV, Gram-Schmidt in one persistent
+ * kernel per inner iteration (classical with selective reorthogonalization by default, or
+ * modified: hec_set_gram_schmidt; deterministic fixed-order grid-wide reductions), Givens
+ * rotations.  Each of the nrhs right-hand sides (row-major n x nrhs, nrhs <= 16) has its
  * own Krylov space; their kernels run batched.  x holds x0 on entry (zero it for x0 = 0) and the
  * solution on exit.  Convergence: the Arnoldi estimate |g_{j+1}| <= rtol ||b|| ends a cycle,
  * then the true residual ||b - A x|| is computed and checked; max_iters bounds the inner

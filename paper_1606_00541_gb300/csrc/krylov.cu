@@ -29,6 +29,7 @@ namespace cg = cooperative_groups;
 namespace hec {
 namespace {
 
+int g_gs_mode = HEC_GS_CLASSICAL;  // process-wide Gram-Schmidt variant (hec_set_gram_schmidt)
 constexpr int kThreads = 256;
 constexpr int kMgsThreads = 1024;  // the persistent Arnoldi kernel: few, large blocks, so that the
                                    // per-projection sum over the blocks' partials stays short
@@ -190,46 +191,58 @@ struct ArnoldiState {
     double* bnorm; // [K]
     int* active;   // [K]
     int* jq;       // [K]  columns used by each right-hand side in this cycle
-    int* reorth;   // [1]  second pass needed
+    int* reorth;   // [1]  Arnoldi steps that took a second Gram-Schmidt pass in this solve
     int* any;      // [1]  some right-hand side still active after this iteration
 };
 
-// Hessenberg column j of right-hand side q from the projections st.h1[0..j] and the norm hn
-// of the orthogonalized vector: previous Givens rotations, the new rotation, the residual
-// estimate g and the convergence test; f = 1 / hn while the right-hand side stays active.
-// Returns whether it is still active.
-__device__ bool arnoldi_column(const ArnoldiState& st, int K, int j, int m, double rtol, int q, double hn) {
-    if (!st.active[q]) {
-        st.f[q] = 0.0;
-        return false;
+// Hessenberg column j of right-hand side q: the projections h_a = hq[a * hs] (+ h2q[a * hs] when
+// a second Gram-Schmidt pass ran), a <= j, and the norm hn of the orthogonalized vector; the
+// previous Givens rotations are applied with a running carry, then the new rotation, the residual
+// estimate g and the convergence test.  Returns the scale 1 / hn of the next basis vector (0 once
+// the right-hand side finishes) and sets *live.  gj and act are g_j and the active flag as they
+// stood when the Arnoldi step began.  Only a caller with `write` set stores the column, the
+// rotation, g, the column count, the active flag and the scale; every caller computes the same
+// result from the same inputs.  With `negated` the arrays hold -h (and -h2).
+__device__ double arnoldi_col(const ArnoldiState& st, int K, int j, int m, double rtol, int q, const double* hq,
+                              const double* h2q, int hs, double hn, double gj, bool act, bool write, bool* live,
+                              bool negated = false) {
+    *live = false;
+    if (!act) {
+        if (write) st.f[q] = 0.0;
+        return 0.0;
     }
-    {
-        {
-            double* H = st.H;
-            for (int a = 0; a <= j; ++a) H[((size_t)a * m + j) * K + q] = st.h1[a * K + q];
-            H[((size_t)(j + 1) * m + j) * K + q] = hn;
-            for (int a = 0; a < j; ++a) {
-                const double c = st.cs[a * K + q], s = st.sn[a * K + q];
-                const double h0 = H[((size_t)a * m + j) * K + q], h1 = H[((size_t)(a + 1) * m + j) * K + q];
-                H[((size_t)a * m + j) * K + q] = c * h0 + s * h1;
-                H[((size_t)(a + 1) * m + j) * K + q] = -s * h0 + c * h1;
-            }
-            const double h0 = H[((size_t)j * m + j) * K + q], h1 = hn;
-            const double den = sqrt(h0 * h0 + h1 * h1);
-            const double c = den == 0.0 ? 1.0 : h0 / den, s = den == 0.0 ? 0.0 : h1 / den;
-            st.cs[j * K + q] = c;
-            st.sn[j * K + q] = s;
-            H[((size_t)j * m + j) * K + q] = c * h0 + s * h1;
-            const double gj = st.g[j * K + q];
-            st.g[(j + 1) * K + q] = -s * gj;
-            st.g[j * K + q] = c * gj;
-            st.jq[q] = j + 1;
-            const bool done = fabs(st.g[(j + 1) * K + q]) <= rtol * st.bnorm[q] || hn == 0.0 || j + 1 >= m;
-            if (done) st.active[q] = 0;
-            st.f[q] = (!done && hn > 0.0) ? 1.0 / hn : 0.0;
-            return !done;
-        }
+    // negated: hq and h2q hold -h and -h2 (negation and the sum of two negated values are exact)
+    auto hval = [&](int a) {
+        const double v = h2q ? hq[a * hs] + h2q[a * hs] : hq[a * hs];
+        return negated ? -v : v;
+    };
+    double* H = st.H;
+    double t = hval(0);
+    for (int a = 0; a < j; ++a) {
+        const double c = st.cs[a * K + q], s = st.sn[a * K + q];
+        const double h1 = hval(a + 1);
+        const double r = c * t + s * h1;
+        t = -s * t + c * h1;
+        if (write) H[((size_t)a * m + j) * K + q] = r;
     }
+    const double den = sqrt(t * t + hn * hn);
+    const double c = den == 0.0 ? 1.0 : t / den, s = den == 0.0 ? 0.0 : hn / den;
+    const double gnext = -s * gj;
+    const bool done = fabs(gnext) <= rtol * st.bnorm[q] || hn == 0.0 || j + 1 >= m;
+    const double f = (!done && hn > 0.0) ? 1.0 / hn : 0.0;
+    if (write) {
+        H[((size_t)j * m + j) * K + q] = c * t + s * hn;
+        H[((size_t)(j + 1) * m + j) * K + q] = hn;
+        st.cs[j * K + q] = c;
+        st.sn[j * K + q] = s;
+        st.g[(j + 1) * K + q] = gnext;
+        st.g[j * K + q] = c * gj;
+        st.jq[q] = j + 1;
+        if (done) st.active[q] = 0;
+        st.f[q] = f;
+    }
+    *live = !done;
+    return f;
 }
 
 // One Arnoldi step after w = A z_j, as one cooperative persistent launch: modified
@@ -311,7 +324,10 @@ __global__ void __launch_bounds__(kMgsThreads) k_arnoldi_mgs(int n, int K, int j
         if (threadIdx.x == 0) any = 0;
         __syncthreads();
         if (threadIdx.x < K) {
-            const bool live = arnoldi_column(st, K, j, m, rtol, threadIdx.x, sqrt(fmax(hsh[threadIdx.x], 0.0)));
+            const int qq = threadIdx.x;
+            bool live;
+            arnoldi_col(st, K, j, m, rtol, qq, st.h1 + qq, nullptr, K, sqrt(fmax(hsh[qq], 0.0)), st.g[j * K + qq],
+                        st.active[qq] != 0, true, &live);
             if (live) atomicOr(&any, 1);
         }
         __syncthreads();
@@ -321,6 +337,272 @@ __global__ void __launch_bounds__(kMgsThreads) k_arnoldi_mgs(int n, int K, int j
     const double f = qa ? st.f[q] : 0.0;
     if (qa)
         for (long r = r0; r < n; r += rs) w[r * K + q] *= f;
+}
+
+// --- Classical Gram-Schmidt with selective reorthogonalization -------------------------------
+//
+// In exact arithmetic classical and modified Gram-Schmidt give the same Hessenberg column and
+// basis vector.  Classical Gram-Schmidt takes all inner products h = V^T w from the same w, so the
+// Arnoldi step needs one grid-wide reduction instead of one per projection, with the same count of
+// FP64 operations.  Its weakness is the loss of orthogonality when the projection cancels most of
+// w; the remedy is a second pass (Daniel, Gragg, Kaufman and Stewart 1976; "twice is enough",
+// Giraud, Langou and Rozloznik 2005) taken only for right-hand sides whose norm fell below
+// eta ||w||.  The norm after the pass follows from Pythagoras, ||w - V h||^2 = ||w||^2 - ||h||^2;
+// the pass itself keeps ||w - V h||^2 >= eta^2 ||w||^2 whenever the formula is used, so it loses
+// at most a few units of rounding to cancellation.
+
+constexpr int kCgsGroup = 8;  // inner products accumulated in one pass over a thread's rows
+// Second pass when ||w - V h|| < eta ||w||.  The textbook choice 1/sqrt(2) asks for it in nearly
+// every step of ILU(0)-FGMRES on the log-normal FV matrices (a step keeps about 0.4 of ||w||, since
+// A M^-1 is close to the identity), which doubles the FP64 work; 0.25 asks for it in 2 of 137 steps
+// at 128^3 with the same iterations and residuals as modified Gram-Schmidt.
+constexpr double kCgsEta = 0.25;
+
+// Block sum of acc[0..G) for each right-hand side: the block's partial for projection a0 + g lands
+// in partial[((a0 + g) * nb + block) * KP + q] for g < na.  red is [32][G][KP] shared memory.
+// Inside a warp the G sums are reduced by recursive halving: at each of the first H lane bits a lane
+// keeps half of its values and adds its partner's copy of that half, so a lane adds 4 + 2 + 1
+// values instead of 3 x 8, then the remaining lane bits (those above log2 KP) are summed on the one
+// value left.  GB300 issues FP64 additions at the FP64 FMA rate, so this halves the warp's FP64
+// instructions per reduction.  The order of the additions is fixed, and every block uses it.
+template <int KP, int G>
+__device__ __forceinline__ void block_partials(double (&acc)[G], double (*red)[G][KP], int a0, int na,
+                                               double* partial, int nb) {
+    static_assert(G == 8, "the halving below is written for 8 sums");
+    constexpr int LK = KP == 1 ? 0 : KP == 2 ? 1 : KP == 4 ? 2 : KP == 8 ? 3 : 4;
+    constexpr int B = 5 - LK;           // lane bits that hold rows of the same right-hand side
+    constexpr int H = B < 3 ? B : 3;    // halving steps
+    constexpr int R = G >> H;           // values a lane holds after them
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double v[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) v[g] = acc[g];
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        const int o = 16 >> h;
+        const bool up = (lane & o) != 0;
+        const int half = G >> (h + 1);
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const double send = up ? v[i] : v[i + half];
+            const double keep = up ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+#pragma unroll
+    for (int o = 16 >> H; o >= KP; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+    // lane L holds sums g = hb * R + i, hb = its H top lane bits (bit 4 first)
+    const int hb = (lane >> (5 - H)) & ((1 << H) - 1);
+    if (((lane >> LK) & ((1 << (B - H)) - 1)) == 0) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) red[warp][hb * R + i][lane & (KP - 1)] = v[i];
+    }
+    __syncthreads();
+    if (threadIdx.x < G * KP) {
+        const int g = threadIdx.x / KP, qq = threadIdx.x % KP;
+        double s = 0.0;
+        for (int wi = 0; wi < kMgsThreads / 32; ++wi) s += red[wi][g][qq];
+        if (g < na) partial[((long)(a0 + g) * nb + blockIdx.x) * KP + qq] = s;
+    }
+    __syncthreads();
+}
+
+// One group of NA inner products over this thread's rows: acc[g] += <V_{a0+g}, x>, where index np
+// stands for x itself (<x, x>).  NA is exact, so no FMA of the loop is predicated off: GB300's FP64
+// pipe spends the same cycles on a warp's FMA whether all of its lanes are on or none.
+template <int NA, int KP>
+__device__ __forceinline__ void cgs_dots_group(int n, int K, const double* __restrict__ V, long vstride,
+                                               const double* x, int np, int a0, double (&acc)[kCgsGroup], long r0,
+                                               long rs, int q) {
+    for (long r = r0; r < n; r += rs) {
+        const double xr = x[r * K + q];
+#pragma unroll
+        for (int g = 0; g < NA; ++g) {
+            const int a = a0 + g;
+            const double va = a < np ? __ldg(V + (long)a * vstride + r * K + q) : xr;
+            acc[g] = fma(va, xr, acc[g]);
+        }
+    }
+}
+
+// Partials of <V_a, x> for a < np and, at index np, of <x, x>, over this thread's rows (r0 + i rs)
+// for its right-hand side q; lanes with `on` false contribute zeros.
+template <int KP>
+__device__ void cgs_dots(int n, int K, const double* __restrict__ V, long vstride, const double* x, int np,
+                         double* partial, int nb, double (*red)[kCgsGroup][KP], long r0, long rs, int q, bool on) {
+    constexpr int G = kCgsGroup;
+    for (int a0 = 0; a0 <= np; a0 += G) {
+        double acc[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) acc[g] = 0.0;
+        const int na = min(G, np + 1 - a0);
+        if (on) {
+            switch (na) {
+                case 1: cgs_dots_group<1, KP>(n, K, V, vstride, x, np, a0, acc, r0, rs, q); break;
+                case 2: cgs_dots_group<2, KP>(n, K, V, vstride, x, np, a0, acc, r0, rs, q); break;
+                case 3: cgs_dots_group<3, KP>(n, K, V, vstride, x, np, a0, acc, r0, rs, q); break;
+                case 4: cgs_dots_group<4, KP>(n, K, V, vstride, x, np, a0, acc, r0, rs, q); break;
+                case 5: cgs_dots_group<5, KP>(n, K, V, vstride, x, np, a0, acc, r0, rs, q); break;
+                case 6: cgs_dots_group<6, KP>(n, K, V, vstride, x, np, a0, acc, r0, rs, q); break;
+                case 7: cgs_dots_group<7, KP>(n, K, V, vstride, x, np, a0, acc, r0, rs, q); break;
+                default: cgs_dots_group<8, KP>(n, K, V, vstride, x, np, a0, acc, r0, rs, q); break;
+            }
+        }
+        block_partials<KP, G>(acc, red, a0, na, partial, nb);
+    }
+}
+
+// hs[a * KP + q] = sum over the nb blocks of partial[a][block][q], a < count, in a fixed order
+// that every block repeats exactly (so all blocks hold bitwise the same sums).
+template <int KP>
+__device__ void cgs_grid_sums(int count, int K, const double* partial, int nb, double* hs) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int idx = warp; idx < count * KP; idx += kMgsThreads / 32) {
+        const int a = idx / KP, qq = idx % KP;
+        double s = 0.0;
+        if (qq < K)
+            for (int b = lane; b < nb; b += 32) s += partial[((long)a * nb + b) * KP + qq];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) hs[idx] = s;
+    }
+    __syncthreads();
+}
+
+// One Arnoldi step after w = A z_j as one cooperative persistent launch: h = V^T w and ||w||^2
+// (one grid-wide reduction), per right-hand side the choice of a second pass, w -= V h, and for
+// the right-hand sides that need it h2 = V^T w, w -= V h2 (a second reduction); the Hessenberg
+// column with h (+ h2), the rotations and the convergence test (stored by block 0, computed
+// identically by every block), and w /= h_{j+1,j} fused into the last pass.  Dynamic shared
+// memory: 2 (j + 2) KP doubles.  partial holds two regions of (m + 2) nb KP doubles.
+template <int KP>
+__global__ void __launch_bounds__(kMgsThreads) k_arnoldi_cgs(int n, int K, int j, int m, double rtol, double eta2,
+                                                          const double* __restrict__ V, long vstride, double* w,
+                                                          double* partial, ArnoldiState st) {
+    cg::grid_group grid = cg::this_grid();
+    constexpr int RPB = kMgsThreads / KP;
+    __shared__ double red[kMgsThreads / 32][kCgsGroup][KP];
+    __shared__ double psh[KP], fsh[KP];
+    __shared__ int resh[KP];
+    __shared__ int any;
+    extern __shared__ double dyn[];
+    const int np = j + 1;
+    double* hs = dyn;                          // [(np + 1) * KP]: h_a, then ||w||^2 at index np
+    double* h2s = dyn + (size_t)(np + 1) * KP;  // the second pass's
+    const int q = threadIdx.x % KP;
+    const bool qa = q < K;
+    const long r0 = (long)blockIdx.x * RPB + threadIdx.x / KP;
+    const long rs = (long)gridDim.x * RPB;
+    const int nb = gridDim.x;
+    double* part2 = partial + (size_t)(m + 2) * nb * KP;
+    // block 0 rewrites g_j and the active flags after the first grid synchronisation
+    double gj = 0.0;
+    bool act = false;
+    if (threadIdx.x < K) {
+        gj = st.g[j * K + threadIdx.x];
+        act = st.active[threadIdx.x] != 0;
+    }
+    if (threadIdx.x == 0) any = 0;
+
+    cgs_dots<KP>(n, K, V, vstride, w, np, partial, nb, red, r0, rs, q, qa);
+    grid.sync();
+    cgs_grid_sums<KP>(np + 1, K, partial, nb, hs);
+    if (threadIdx.x < KP) {
+        int re = 0;
+        double p = 0.0;
+        if (threadIdx.x < K) {
+            const double s = hs[np * KP + threadIdx.x];
+            double hh = 0.0;
+            for (int a = 0; a < np; ++a) hh = fma(hs[a * KP + threadIdx.x], hs[a * KP + threadIdx.x], hh);
+            p = s - hh;
+            re = act && s > 0.0 && p < eta2 * s;
+        }
+        psh[threadIdx.x] = p;
+        resh[threadIdx.x] = re;
+    }
+    __syncthreads();
+    bool second = false;
+    for (int qq = 0; qq < K; ++qq) second = second || resh[qq] != 0;
+    // the passes below subtract h: keep -h, so that each FMA takes it as it is
+    for (int i = threadIdx.x; i < np * KP; i += kMgsThreads) hs[i] = -hs[i];
+    __syncthreads();
+
+    if (!second) {
+        if (threadIdx.x < K) {
+            bool live;
+            fsh[threadIdx.x] = arnoldi_col(st, K, j, m, rtol, threadIdx.x, hs + threadIdx.x, nullptr, KP,
+                                           sqrt(fmax(psh[threadIdx.x], 0.0)), gj, act, blockIdx.x == 0, &live, true);
+            if (live) atomicOr(&any, 1);
+        }
+        __syncthreads();
+        if (blockIdx.x == 0 && threadIdx.x == 0) *st.any = any;
+        if (qa) {
+            const double f = fsh[q];
+            for (long r = r0; r < n; r += rs) {
+                double wr = w[r * K + q];
+#pragma unroll 4
+                for (int a = 0; a < np; ++a) wr = fma(hs[a * KP + q], __ldg(V + (long)a * vstride + r * K + q), wr);
+                w[r * K + q] = wr * f;
+            }
+        }
+        return;
+    }
+
+    // w -= V h for every right-hand side, then the second pass's inner products where it is needed
+    const bool re = qa && resh[q] != 0;
+    if (qa)
+        for (long r = r0; r < n; r += rs) {
+            double wr = w[r * K + q];
+#pragma unroll 4
+            for (int a = 0; a < np; ++a) wr = fma(hs[a * KP + q], __ldg(V + (long)a * vstride + r * K + q), wr);
+            w[r * K + q] = wr;
+        }
+    cgs_dots<KP>(n, K, V, vstride, w, np, part2, nb, red, r0, rs, q, re);
+    grid.sync();
+    cgs_grid_sums<KP>(np + 1, K, part2, nb, h2s);
+    if (threadIdx.x < K) {
+        const int qq = threadIdx.x;
+        double hn = sqrt(fmax(psh[qq], 0.0));
+        if (resh[qq]) {
+            const double s2 = h2s[np * KP + qq];
+            double hh = 0.0;
+            for (int a = 0; a < np; ++a) hh = fma(h2s[a * KP + qq], h2s[a * KP + qq], hh);
+            const double p2 = s2 - hh;
+            // a second pass that still cancels most of the vector: w lies in span(V) to working
+            // precision (breakdown; the Krylov space is invariant)
+            hn = p2 < eta2 * s2 ? 0.0 : sqrt(p2);
+        }
+        psh[qq] = hn;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < np * KP; i += kMgsThreads) h2s[i] = -h2s[i];
+    __syncthreads();
+    if (threadIdx.x < K) {
+        const int qq = threadIdx.x;
+        bool live;
+        fsh[qq] = arnoldi_col(st, K, j, m, rtol, qq, hs + qq, resh[qq] ? h2s + qq : nullptr, KP, psh[qq], gj, act,
+                              blockIdx.x == 0, &live, true);
+        if (live) atomicOr(&any, 1);
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *st.any = any;
+        *st.reorth += 1;
+    }
+    if (qa) {
+        const double f = fsh[q];
+        for (long r = r0; r < n; r += rs) {
+            double wr = w[r * K + q];
+            if (re) {
+#pragma unroll 4
+                for (int a = 0; a < np; ++a) wr = fma(h2s[a * KP + q], __ldg(V + (long)a * vstride + r * K + q), wr);
+            }
+            w[r * K + q] = wr * f;
+        }
+    }
 }
 
 // y = R^-1 g on each right-hand side's rotated Hessenberg; zero beyond its column count
@@ -375,38 +657,58 @@ struct Dots {
     }
 };
 
-// Launcher of the persistent Arnoldi kernel: grid = resident blocks (cooperative launch).
+// Launcher of the persistent Arnoldi kernels: grid = resident blocks (cooperative launch).
 struct Mgs {
     double* partial = nullptr;
     int cap_blocks = 0;
-    hec_status init() {
+    int m = 0;
+    int mode = HEC_GS_CLASSICAL;
+    hec_status init(int restart, int gs_mode) {
         cap_blocks = num_sms() * (2048 / kMgsThreads);
-        return dalloc(&partial, (size_t)2 * cap_blocks * 16);
+        m = restart;
+        mode = gs_mode;
+        // MGS: two single-slot buffers; CGS: two regions of (m + 2) projections
+        return dalloc(&partial, (size_t)2 * (m + 2) * cap_blocks * 16);
     }
     ~Mgs() { cudaFree(partial); }
     template <int KP>
-    hec_status run_kp(int n, int K, int j, int m, double rtol, const double* V, long vstride, double* w,
+    hec_status run_kp(int n, int K, int j, double rtol, const double* V, long vstride, double* w,
                       ArnoldiState& st, cudaStream_t s) {
-        const void* k = (const void*)k_arnoldi_mgs<KP>;
-        static int per_sm = -1;  // per template instance
-        if (per_sm < 0) per_sm = max_coop_blocks(k, kMgsThreads, 0);
-        if (per_sm <= 0) return set_error(HEC_ERR_CUDA, "Arnoldi kernel cannot be resident");
+        const bool cgs = mode == HEC_GS_CLASSICAL;
+        const void* k = cgs ? (const void*)k_arnoldi_cgs<KP> : (const void*)k_arnoldi_mgs<KP>;
+        // dynamic shared memory of the classical kernel: h and h2 for up to 256 + 2 projections
+        const size_t smem_max = cgs ? (size_t)2 * (256 + 2) * KP * sizeof(double) : 0;
+        static int per_sm[2] = {-1, -1};  // per template instance and kernel
+        int& ps = per_sm[cgs ? 1 : 0];
+        if (ps < 0) {
+            if (cgs) HEC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+            ps = max_coop_blocks(k, kMgsThreads, smem_max);
+        }
+        if (ps <= 0) return set_error(HEC_ERR_CUDA, "Arnoldi kernel cannot be resident");
         const long want = ((long)n * KP + kMgsThreads - 1) / kMgsThreads;
-        int blocks = (int)std::max(1L, std::min<long>(std::min(per_sm * num_sms(), cap_blocks), want));
+        int blocks = (int)std::max(1L, std::min<long>(std::min(ps * num_sms(), cap_blocks), want));
         double* part = partial;
-        void* args[] = {&n, &K, &j, &m, &rtol, (void*)&V, &vstride, &w, &part, &st};
+        int mm = m;
         ProfScope ps_(s, PROF_GS);
-        HEC_CUDA(cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(kMgsThreads), args, 0, s));
+        if (cgs) {
+            double eta2 = kCgsEta * kCgsEta;
+            const size_t smem = (size_t)2 * (j + 2) * KP * sizeof(double);
+            void* args[] = {&n, &K, &j, &mm, &rtol, &eta2, (void*)&V, &vstride, &w, &part, &st};
+            HEC_CUDA(cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(kMgsThreads), args, smem, s));
+        } else {
+            void* args[] = {&n, &K, &j, &mm, &rtol, (void*)&V, &vstride, &w, &part, &st};
+            HEC_CUDA(cudaLaunchCooperativeKernel(k, dim3(blocks), dim3(kMgsThreads), args, 0, s));
+        }
         count_launch();
         return HEC_OK;
     }
-    hec_status run(int n, int K, int j, int m, double rtol, const double* V, long vstride, double* w,
+    hec_status run(int n, int K, int j, double rtol, const double* V, long vstride, double* w,
                    ArnoldiState& st, cudaStream_t s) {
-        if (K <= 1) return run_kp<1>(n, K, j, m, rtol, V, vstride, w, st, s);
-        if (K <= 2) return run_kp<2>(n, K, j, m, rtol, V, vstride, w, st, s);
-        if (K <= 4) return run_kp<4>(n, K, j, m, rtol, V, vstride, w, st, s);
-        if (K <= 8) return run_kp<8>(n, K, j, m, rtol, V, vstride, w, st, s);
-        return run_kp<16>(n, K, j, m, rtol, V, vstride, w, st, s);
+        if (K <= 1) return run_kp<1>(n, K, j, rtol, V, vstride, w, st, s);
+        if (K <= 2) return run_kp<2>(n, K, j, rtol, V, vstride, w, st, s);
+        if (K <= 4) return run_kp<4>(n, K, j, rtol, V, vstride, w, st, s);
+        if (K <= 8) return run_kp<8>(n, K, j, rtol, V, vstride, w, st, s);
+        return run_kp<16>(n, K, j, rtol, V, vstride, w, st, s);
     }
 };
 
@@ -681,6 +983,16 @@ HEC_API hec_status stage_destroy(hec_stage* S) {
     return HEC_OK;
 }
 
+HEC_API hec_status hec_set_gram_schmidt(int mode) {
+    clear_error();
+    if (mode != HEC_GS_CLASSICAL && mode != HEC_GS_MODIFIED)
+        return set_error(HEC_ERR_INVALID_ARG, "hec_set_gram_schmidt: mode must be HEC_GS_CLASSICAL or HEC_GS_MODIFIED");
+    g_gs_mode = mode;
+    return HEC_OK;
+}
+
+HEC_API int hec_get_gram_schmidt(void) { return g_gs_mode; }
+
 HEC_API hec_status spmv(const hec_matrix* A, int nrhs, double alpha, const double* x, int ldx, double beta, double* y,
                         int ldy, void* stream) {
     clear_error();
@@ -736,7 +1048,7 @@ HEC_API hec_status fgmres_solve(const hec_matrix* A, const ilu_precond* M, const
     hec_status st = HEC_OK;
     if ((st = dalloc(&W.V, (size_t)(m + 1) * nk)) || (st = dalloc(&W.Z, (size_t)m * nk)) ||
         (st = dalloc(&W.small, nsmall)) || (st = dalloc(&W.ints, (size_t)2 * K + 2)) || (st = dots.init(m + 2, K)) ||
-        (st = mgs.init()))
+        (st = mgs.init(m, g_gs_mode)))
         return st;
     HEC_CUDA(cudaHostAlloc((void**)&W.pinned, 2 * sizeof(int), cudaHostAllocDefault));
     HEC_CUDA(cudaEventCreateWithFlags(&W.ev[0], cudaEventDisableTiming));
@@ -760,6 +1072,7 @@ HEC_API hec_status fgmres_solve(const hec_matrix* A, const ilu_precond* M, const
         as.reorth = W.ints + 2 * K;
         as.any = W.ints + 2 * K + 1;
     }
+    HEC_CUDA(cudaMemsetAsync(as.reorth, 0, sizeof(int), s));
     const int gb = grid_for(nk);
     std::vector<double> hb(K), hn(K), g0((size_t)(m + 1) * K), fh(K);
     std::vector<int> act(K), jq(K);
@@ -834,8 +1147,8 @@ HEC_API hec_status fgmres_solve(const hec_matrix* A, const ilu_precond* M, const
                 HEC_CUDA(cudaMemcpyAsync(zj, vj, sizeof(double) * nk, cudaMemcpyDeviceToDevice, s));
             }
             if (!extra || extra->A != A) HEC_CHECK(spmv_impl(A, K, 1.0, zj, K, 0.0, wv, K, s));
-            // modified Gram-Schmidt, ||w||, Hessenberg column, rotations, w /= h_{j+1,j}
-            HEC_CHECK(mgs.run(n, K, j, m, rtol, W.V, nk, wv, as, s));
+            // Gram-Schmidt, ||w||, Hessenberg column, rotations, w /= h_{j+1,j}
+            HEC_CHECK(mgs.run(n, K, j, rtol, W.V, nk, wv, as, s));
             HEC_CUDA(cudaMemcpyAsync(W.pinned + (j & 1), as.any, sizeof(int), cudaMemcpyDeviceToHost, s));
             HEC_CUDA(cudaEventRecord(W.ev[j & 1], s));
             launched = j + 1;
@@ -862,6 +1175,8 @@ HEC_API hec_status fgmres_solve(const hec_matrix* A, const ilu_precond* M, const
         HEC_CUDA(cudaGetLastError());
     }
     HEC_CHECK(check_sweeps());
+    HEC_CUDA(cudaMemcpyAsync(&inf.reorthogonalized, as.reorth, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HEC_CUDA(cudaStreamSynchronize(s));
     inf.iterations = its;
     inf.restarts = restarts;
     inf.converged = all_conv ? 1 : 0;

@@ -48,7 +48,8 @@ class HecTune(ctypes.Structure):
 
 
 class HecFgmresInfo(ctypes.Structure):
-    _fields_ = [("iterations", _i), ("restarts", _i), ("converged", _i), ("rel_residual", _d), ("seconds", _d)]
+    _fields_ = [("iterations", _i), ("restarts", _i), ("converged", _i), ("rel_residual", _d), ("seconds", _d),
+                ("reorthogonalized", _i)]
 
 
 def _sig(name, *args):
@@ -163,6 +164,21 @@ def launch_count():
 
 def library_path():
     return LIB_PATH
+
+
+GS_CLASSICAL, GS_MODIFIED = 0, 1
+_hec_set_gram_schmidt = _sig("hec_set_gram_schmidt", _i)
+
+
+def set_gram_schmidt(mode):
+    """Gram-Schmidt variant of fgmres_solve's Arnoldi step, process-wide: "classical" (with
+    selective reorthogonalization, the default) or "modified" (hec_set_gram_schmidt)."""
+    code = {"classical": GS_CLASSICAL, "modified": GS_MODIFIED}[mode]
+    _check(_hec_set_gram_schmidt(code), "hec_set_gram_schmidt")
+
+
+def get_gram_schmidt():
+    return {GS_CLASSICAL: "classical", GS_MODIFIED: "modified"}[_lib.hec_get_gram_schmidt()]
 
 
 class _DevArray:
@@ -410,7 +426,7 @@ def fgmres_solve(A, M, b, x=None, restart=30, rtol=1e-8, max_iters=1000, stream=
     if st != OK and not (st == NOT_CONVERGED and not raise_on_nonconvergence):
         raise HecError(st, "fgmres_solve")
     return x, dict(iterations=info.iterations, restarts=info.restarts, converged=bool(info.converged),
-                   rel_residual=info.rel_residual, seconds=info.seconds)
+                   rel_residual=info.rel_residual, seconds=info.seconds, reorthogonalized=info.reorthogonalized)
 
 
 def ilu_factor(rowptr, col, val, k=0, stream=None):
