@@ -328,10 +328,9 @@ def main():
     # roofline of the dominant kernel (the sweep) from its live CUDA-event durations
     hbm, src = peaks()
     per_sweep = 0.5 * (sweep_bytes(nnzL, n, 1, 4) + sweep_bytes(nnzU, n, 1, 4))
-    if args.sweep == "part":
-        # the partitioned kernel reads the right-hand side already gathered into plan order in
-        # FP32 (k_part_prep does the FP64 gather before it): 4 of the 8 bytes a row
-        per_sweep -= 4 * n
+    # the ILU apply keeps its intermediate y in FP32 with FP32 factor values: the lower sweep
+    # writes it and the upper sweep reads it at 4 bytes a row instead of 8 (4 bytes less a sweep)
+    per_sweep -= 4 * n
     avg_launch_s = (sweep_ms / 1000.0) / max(sweep_launches, 1)
     achieved = per_sweep / avg_launch_s / 1e9
     step_s = elapsed / args.steps

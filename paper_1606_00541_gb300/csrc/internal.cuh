@@ -110,6 +110,14 @@ struct hec_part_data {
     int nchunks = 0;
     int max_rows = 0;           // rows of the largest part (its shared-memory solution)
     int threads = 256;
+    // Two plan-order solution buffers (the cross-part words): a sweep polls xpb[parity] and sets
+    // the other one to the sentinel for the next sweep, so no fill runs between sweeps.  Sweeps of
+    // one plan are stream-ordered (as for every plan), which is what makes the other buffer idle.
+    void* xpb[2] = {nullptr, nullptr};
+    mutable int parity = 0;
+    long long id = 0;           // unique per partition build (caches of composed indices key on it)
+    int* pos = nullptr;         // [n] row of the level-ordered factor -> plan row (inverse of rowg)
+    int* bidx_perm = nullptr;   // [n] plan row -> row of b for sptrsv_lower / sptrsv_upper (iperm[rowg])
 };
 
 struct sptrsv_plan {
@@ -140,6 +148,12 @@ struct ilu_precond {
     void* y = nullptr;         // [n_ext * max_nrhs] intermediate, already in the upper factor's order
     bool y32 = false;          // y in FP32 (both sweeps compute in FP32), else FP64
     int max_nrhs = 1;
+    // composed indices for partitioned single-right-hand-side sweeps, built at the first apply
+    // after a partition changes (keyed on hec_part_data::id):
+    mutable int* lg_part = nullptr;     // [n_ext] plan row of L -> row of r (l_gather[rowg_L])
+    mutable long long lg_part_id = 0;
+    mutable int* ls_upart = nullptr;    // [n_ext] level row of L -> plan row of U (pos_U[l_scatter])
+    mutable long long ls_upart_id = 0;
 };
 
 struct hec_csr {
@@ -182,8 +196,12 @@ inline int default_lanes_per_row(const hec_matrix* T) {
 
 // sweep launcher shared by sptrsv_* and ilu_apply: gather[r] is the row of b feeding new row r
 // (NULL = identity), scatter[r] the row of x receiving it (NULL = identity, -1 = skip).
+// For a partitioned single-right-hand-side sweep, bidx (if not NULL) gives the row of b for each
+// plan row directly (a gather composed with the plan's row order), and bplan says b is already in
+// the plan's row order; both are ignored on the other paths.
 hec_status sweep(const sptrsv_plan* p, int nrhs, const double* b, int ldb, const int* gather, double* x,
-                 int ldx, const int* scatter, cudaStream_t s, bool b32 = false, bool x32 = false);
+                 int ldx, const int* scatter, cudaStream_t s, bool b32 = false, bool x32 = false,
+                 const int* bidx = nullptr, bool bplan = false);
 // y = alpha A x + beta y for a general-mode FP64 HEC matrix (krylov.cu; no argument checks)
 hec_status spmv_impl(const hec_matrix* A, int K, double alpha, const double* x, int ldx, double beta, double* y,
                      int ldy, cudaStream_t s);

@@ -20,6 +20,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <atomic>
+
 #include "internal.cuh"
 #include "sync.cuh"
 
@@ -639,14 +641,17 @@ struct PartParams {
     const int* __restrict__ part_row;
     const int* __restrict__ part_chunk;
     const int2* __restrict__ chunks;
-    const void* __restrict__ bp;  // b gathered into plan order in the work type (k_part_prep)
+    void* bp;  // b gathered into plan order in the work type (by each part, in the sweep's prologue)
     const double* __restrict__ b;
     int ldb;
     const int* __restrict__ gather;
     double* __restrict__ x;
     int ldx;
     const int* __restrict__ scatter;
-    void* xp;
+    void* xp;       // plan-order solution words polled by this sweep (set to the sentinel before it)
+    void* xp_next;  // the other buffer: set to the sentinel here for the next sweep
+    const int* __restrict__ bidx;  // plan row -> row of b (NULL: gather[rowg] or rowg)
+    int bplan;                     // b already in plan order
     int* status;
     long long budget;
     int skip_row;
@@ -771,10 +776,10 @@ struct DepBatchP {
 
 // One lane's row of a chunk of the partitioned sweep: everything but the dependencies, loaded
 // for the warp's next chunk while it waits on the current one.  The loads are all one step from
-// the row index (the right-hand side is gathered into plan order before the sweep) and nothing
-// here uses a loaded value: widening, the tail length and the scatter index are derived when the
-// chunk is processed, so issuing the prefetch never stalls the warp.  Slab values are loaded
-// whether or not the slot is padding (padding is in bounds and zero).
+// the row index (the right-hand side is gathered into plan order in the sweep's prologue) and
+// nothing here uses a loaded value: widening, the tail length and the scatter index are derived
+// when the chunk is processed, so issuing the prefetch never stalls the warp.  Slab values are
+// loaded whether or not the slot is padding (padding is in bounds and zero).
 
 template <typename VT, typename XT, typename AT, int NP>
 struct PartRow {
@@ -797,10 +802,12 @@ struct PartRow {
         if (have && lane < ch.y) {
             const int r = ch.x + lane;
             g = __ldg(p.rowg + r);
-            if (sizeof(AT) == 4) {
-                b = __ldg((const AT*)p.bp + r);
+            if (p.bplan) {
+                b = ld_rhs<AT>(p.b, p.b32, (long)r * p.ldb);
+            } else if (sizeof(AT) == 4) {
+                b = __ldcg((const AT*)p.bp + r);  // written by this block in the prologue: not the read-only path
             } else {  // FP64: gathered here (the row is loaded when its chunk starts)
-                const int gr = p.gather ? __ldg(p.gather + g) : g;
+                const int gr = p.bidx ? __ldg(p.bidx + r) : p.gather ? __ldg(p.gather + g) : g;
                 b = ld_rhs<AT>(p.b, p.b32, (long)gr * p.ldb);
             }
             t0 = __ldg(p.tptr + r);
@@ -818,21 +825,6 @@ struct PartRow {
     }
 };
 
-// Before a partitioned sweep: the level-ordered solution set to the sentinel, and the right-hand
-// side gathered into plan order in the work type.
-template <typename XT>
-__global__ void k_part_prep(int n, XT* xp, const int* __restrict__ rowg, const int* __restrict__ gather,
-                            const double* __restrict__ b, int ldb, int b32, typename Acc<XT>::T* bp) {
-    const int st = gridDim.x * blockDim.x;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) {
-        if (sizeof(XT) == 8) ((unsigned long long*)xp)[i] = kSent64;
-        else ((unsigned int*)xp)[i] = kSent32;
-        const int g = __ldg(rowg + i);
-        const int gr = gather ? __ldg(gather + g) : g;
-        bp[i] = ld_rhs<typename Acc<XT>::T>(b, b32, (long)gr * ldb);
-    }
-}
-
 template <typename VT, typename XT, int WMAX>
 __global__ void __launch_bounds__(1024, 1) k_sweep_part(PartParams p) {
     typedef typename Acc<XT>::T AT;
@@ -842,17 +834,49 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_part(PartParams p) {
     // registers of a 1024-thread block (64 a thread) would otherwise spill
     constexpr int NP = WMAX > 4 ? 0 : sizeof(AT) == 8 ? 2 : WMAX;
     // FP32 work: the next chunk's row is loaded while the current one waits, and the right-hand
-    // side comes gathered by k_part_prep.  FP64 work: a level is long enough (FP64 arithmetic on
-    // the chain) that loading the row, right-hand side gather included, when the chunk starts
-    // costs nothing, while a gathering pass before the sweep would.
+    // side is gathered into plan order in the prologue.  FP64 work: a level is long enough (FP64
+    // arithmetic on the chain) that loading the row, right-hand side gather included, when the
+    // chunk starts costs nothing, while a gathering step before the sweep would.
     constexpr bool PF = sizeof(AT) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WT* sxp = (WT*)smem_raw;
     const unsigned int sbase = (unsigned int)__cvta_generic_to_shared(smem_raw);
     const int part = blockIdx.x;
     const int lo = __ldg(p.part_row + part), hi = __ldg(p.part_row + part + 1);
-    for (int i = threadIdx.x; i < hi - lo; i += blockDim.x) sxp[i] = W::kSent;
-    __syncthreads();
+    // Prologue: the part's rows of the shared solution set to the sentinel and, for FP32 work, the
+    // part's rows of the right-hand side gathered into plan order (read back only by this block).
+    // The global buffer this sweep polls was set to the sentinel by the previous sweep of the plan
+    // (see the epilogue), so no grid-wide synchronisation is needed.
+    {
+        for (int i = threadIdx.x; i < hi - lo; i += blockDim.x) sxp[i] = W::kSent;
+        if (PF && !p.bplan) {
+            // kPro rows a thread at a time, each dependent load issued for all of them before the
+            // next, so a batch costs one memory round trip per step of the index chain
+            constexpr int kPro = 8;
+            AT* bp = (AT*)p.bp;
+            for (int i0 = 0; i0 < hi - lo; i0 += kPro * (int)blockDim.x) {
+                int gi[kPro];
+                AT bv[kPro];
+#pragma unroll
+                for (int u = 0; u < kPro; ++u) {
+                    const int i = i0 + u * (int)blockDim.x + (int)threadIdx.x;
+                    gi[u] = i < hi - lo ? __ldg((p.bidx ? p.bidx : p.rowg) + lo + i) : -1;
+                }
+                if (p.gather && !p.bidx) {
+#pragma unroll
+                    for (int u = 0; u < kPro; ++u) gi[u] = gi[u] >= 0 ? __ldg(p.gather + gi[u]) : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < kPro; ++u) bv[u] = gi[u] >= 0 ? ld_rhs<AT>(p.b, p.b32, (long)gi[u] * p.ldb) : AT(0);
+#pragma unroll
+                for (int u = 0; u < kPro; ++u) {
+                    const int i = i0 + u * (int)blockDim.x + (int)threadIdx.x;
+                    if (i < hi - lo) bp[lo + i] = bv[u];
+                }
+            }
+        }
+        __syncthreads();
+    }
     const int c0 = __ldg(p.part_chunk + part), c1 = __ldg(p.part_chunk + part + 1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const VT* __restrict__ ev = (const VT*)p.ell_val;
@@ -932,6 +956,11 @@ __global__ void __launch_bounds__(1024, 1) k_sweep_part(PartParams p) {
         if (pub) publish_x(xp + r, (XT)xr);  // consumers in other parts
         if (act && sr >= 0) st_sol(p.x, p.x32, (long)sr * p.ldx, xr);
     }
+    // Epilogue: the part's rows of the other global buffer, which the next sweep of this plan
+    // polls, set to the sentinel (nothing reads that buffer during this sweep; done last, it stays
+    // off the dependency chain).
+    WT* nxp = (WT*)p.xp_next;
+    for (int i = threadIdx.x; i < hi - lo; i += blockDim.x) nxp[lo + i] = W::kSent;
 }
 
 template <typename XT>
@@ -1153,17 +1182,6 @@ template <typename VT, typename XT, int WMAX>
 hec_status launch_part(const sptrsv_plan* pl, PartParams& pp, cudaStream_t s) {
     const hec_part_data* P = pl->part;
     const void* k = (const void*)k_sweep_part<VT, XT, WMAX>;
-    const long count = pl->T->n;
-    const int fb = (int)std::min(4096L, std::max(1L, (count + 255) / 256));
-    {
-        ProfScope ps_(s, PROF_FILL);
-        if (sizeof(typename Acc<XT>::T) == 4)
-            k_part_prep<XT><<<fb, 256, 0, s>>>((int)count, (XT*)pp.xp, P->rowg, pp.gather, pp.b, pp.ldb, pp.b32,
-                                               (typename Acc<XT>::T*)P->bp);
-        else
-            k_fill_sentinel<XT><<<fb, 256, 0, s>>>((XT*)pp.xp, count);
-    }
-    HEC_LAUNCHED();
     void* args[] = {&pp};
     void* tok = nullptr;
     const size_t smem = (size_t)P->max_rows * sizeof(XT);
@@ -1171,6 +1189,7 @@ hec_status launch_part(const sptrsv_plan* pl, PartParams& pp, cudaStream_t s) {
     HEC_CUDA(cudaLaunchCooperativeKernel(k, dim3(P->nparts), dim3(P->threads), args, smem, s));
     profile_end(s, tok);
     count_launch();
+    P->parity ^= 1;  // launched: the next sweep polls the buffer this one sets to the sentinel
     return HEC_OK;
 }
 
@@ -1187,7 +1206,7 @@ const void* part_kernel(int w) {
 }  // namespace
 
 hec_status sweep(const sptrsv_plan* pl, int nrhs, const double* b, int ldb, const int* gather, double* x, int ldx,
-                 const int* scatter, cudaStream_t s, bool b32, bool x32) {
+                 const int* scatter, cudaStream_t s, bool b32, bool x32, const int* bidx, bool bplan) {
     const hec_matrix* T = pl->T;
     if (T->n == 0) return HEC_OK;
     if (pl->part && pl->use_part && nrhs == 1) {
@@ -1213,7 +1232,10 @@ hec_status sweep(const sptrsv_plan* pl, int nrhs, const double* b, int ldb, cons
         pp.x = x;
         pp.ldx = ldx;
         pp.scatter = scatter;
-        pp.xp = pl->xp;
+        pp.xp = P->xpb[P->parity];
+        pp.xp_next = P->xpb[P->parity ^ 1];
+        pp.bidx = bidx ? bidx : (gather && gather == pl->lv->iperm ? P->bidx_perm : nullptr);
+        pp.bplan = bplan;
         pp.status = pl->status;
         pp.budget = pl->wait_cycles;
         pp.skip_row = pl->skip_row;
@@ -1268,6 +1290,29 @@ __global__ void k_ilu_maps(int n, const int* __restrict__ iperm_l, const int* __
     int iu = iperm_u[r];
     us[r] = ext2glob ? (owned[iu] ? ext2glob[iu] : -1) : iu;  // upper sweep writes owned rows only
 }
+// out[i] = outer[inner[i]] (-1 stays -1)
+__global__ void k_compose(int n, const int* __restrict__ inner, const int* __restrict__ outer, int* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int k = inner[i];
+    out[i] = k >= 0 ? outer[k] : -1;
+}
+// The composed indices of partitioned sweeps of M: for the lower factor's partition, the row of r
+// of each plan row (so the sweep's gather is one load); for the upper factor's, the plan row of U
+// that receives each row of y (so the lower sweep writes y in the order the upper sweep reads it).
+hec_status ilu_compose(const ilu_precond* M, const hec_part_data* P, bool lower, cudaStream_t s) {
+    int*& out = lower ? M->lg_part : M->ls_upart;
+    long long& id = lower ? M->lg_part_id : M->ls_upart_id;
+    if (id == P->id) return HEC_OK;
+    if (!out) HEC_CHECK(dalloc(&out, (size_t)M->n_ext));
+    const int n = M->n_ext;
+    if (lower) k_compose<<<(n + 255) / 256, 256, 0, s>>>(n, P->rowg, M->l_gather, out);
+    else k_compose<<<(n + 255) / 256, 256, 0, s>>>(n, M->l_scatter, P->pos, out);
+    count_launch();
+    HEC_CUDA(cudaGetLastError());
+    id = P->id;
+    return HEC_OK;
+}
 }  // namespace
 
 void free_part(hec_part_data* P) {
@@ -1275,6 +1320,7 @@ void free_part(hec_part_data* P) {
     cudaFree(P->rowg); cudaFree(P->part_row); cudaFree(P->part_seg); cudaFree(P->seg_start);
     cudaFree(P->ell_col); cudaFree(P->ell_val); cudaFree(P->tptr); cudaFree(P->tcol); cudaFree(P->tval); cudaFree(P->dinv);
     cudaFree(P->bp); cudaFree(P->part_chunk); cudaFree(P->chunks);
+    cudaFree(P->xpb[0]); cudaFree(P->xpb[1]); cudaFree(P->pos); cudaFree(P->bidx_perm);
     delete P;
 }
 
@@ -1399,6 +1445,15 @@ __global__ void k_perm_dinv(int n, const int* __restrict__ rowg, const XT* __res
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r < n) nd[r] = d[rowg[r]];
 }
+// pos = inverse of rowg; bidx[r] = iperm[rowg[r]] (the row of b of plan row r in sptrsv_lower/upper)
+__global__ void k_part_pos(int n, const int* __restrict__ rowg, const int* __restrict__ iperm, int* pos, int* bidx) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int g = rowg[r];
+    pos[g] = r;
+    bidx[r] = iperm[g];
+}
+std::atomic<long long> g_part_id{0};
 }  // namespace
 
 hec_status build_partition(sptrsv_plan* p, const int* part, int nparts, cudaStream_t s) {
@@ -1467,8 +1522,20 @@ hec_status build_partition(sptrsv_plan* p, const int* part, int nparts, cudaStre
     const size_t ws = T->vdt == HEC_F64 ? 8 : 4;
     if ((st = dalloc(&P->ell_col, (size_t)T->w * T->ld)) || (st = dmalloc(&P->ell_val, vs * (size_t)T->w * T->ld + 16)) ||
         (st = dalloc(&P->tcol, (size_t)T->tail_nnz)) || (st = dmalloc(&P->tval, vs * (size_t)T->tail_nnz + 16)) ||
-        (st = dmalloc(&P->dinv, ws * (size_t)n + 16)) || (ws == 4 && (st = dmalloc(&P->bp, ws * (size_t)n + 16))))
+        (st = dmalloc(&P->dinv, ws * (size_t)n + 16)) || (ws == 4 && (st = dmalloc(&P->bp, ws * (size_t)n + 16))) ||
+        (st = dmalloc(&P->xpb[0], ws * (size_t)n + 16)) || (st = dmalloc(&P->xpb[1], ws * (size_t)n + 16)) ||
+        (st = dalloc(&P->pos, n)) || (st = dalloc(&P->bidx_perm, n)))
         return done(st);
+    P->id = ++g_part_id;
+    k_part_pos<<<g, 256, 0, s>>>(n, P->rowg, lv->iperm, P->pos, P->bidx_perm);
+    count_launch();
+    {
+        // the buffer the first sweep polls; every sweep sets the other one for its successor
+        const int fb = std::min(4096, std::max(1, g));
+        if (ws == 8) k_fill_sentinel<double><<<fb, 256, 0, s>>>((double*)P->xpb[0], n);
+        else k_fill_sentinel<float><<<fb, 256, 0, s>>>((float*)P->xpb[0], n);
+        count_launch();
+    }
     const int gl = (T->ld + 255) / 256;
     if (T->vdt == HEC_F64) {
         k_repack<double><<<gl, 256, 0, s>>>(n, T->ld, T->w, P->rowg, sigma, T->ell_col, (const double*)T->ell_val, T->tptr,
@@ -1805,6 +1872,8 @@ HEC_API hec_status ilu_destroy(ilu_precond* M) {
     cudaFree(M->l_scatter);
     cudaFree(M->u_scatter);
     cudaFree(M->y);
+    cudaFree(M->lg_part);
+    cudaFree(M->ls_upart);
     delete M;
     return HEC_OK;
 }
@@ -1814,8 +1883,16 @@ HEC_API hec_status ilu_apply(const ilu_precond* M, int nrhs, const double* r, in
     if (!M || nrhs < 1 || nrhs > M->max_nrhs || ldr < nrhs || ldz < nrhs || (M->n_glob > 0 && (!r || !z)))
         return set_error(HEC_ERR_INVALID_ARG, "ilu_apply: bad argument");
     cudaStream_t s = S(stream);
-    // L y = r: gather r, write y already permuted into the upper factor's level order
-    HEC_CHECK(sweep(M->L, nrhs, r, ldr, M->l_gather, (double*)M->y, nrhs, M->l_scatter, s, false, M->y32));
+    // partitioned single-right-hand-side sweeps take composed indices: L gathers r with one load
+    // a row, and writes y straight into U's plan order, which U then reads in order
+    const bool lpart = M->L->part && M->L->use_part && nrhs == 1 && M->n_ext > 0;
+    const bool upart = M->U->part && M->U->use_part && nrhs == 1 && M->n_ext > 0;
+    if (lpart) HEC_CHECK(ilu_compose(M, M->L->part, true, s));
+    if (upart) HEC_CHECK(ilu_compose(M, M->U->part, false, s));
+    // L y = r: gather r, write y already permuted into the upper factor's level (or plan) order
+    HEC_CHECK(sweep(M->L, nrhs, r, ldr, M->l_gather, (double*)M->y, nrhs, upart ? M->ls_upart : M->l_scatter, s,
+                    false, M->y32, lpart ? M->lg_part : nullptr));
     // U z = y: y is read in order, z is written back (owned rows only for RAS)
-    return sweep(M->U, nrhs, (const double*)M->y, nrhs, nullptr, z, ldz, M->u_scatter, s, M->y32, false);
+    return sweep(M->U, nrhs, (const double*)M->y, nrhs, nullptr, z, ldz, M->u_scatter, s, M->y32, false, nullptr,
+                 upart);
 }
