@@ -57,6 +57,15 @@ typedef struct hec_csr hec_csr;
 /* Message for the last failing call on this thread ("" when none). */
 const char* hec_last_error(void);
 
+/* Device memory held for reuse.  The library keeps the blocks its handles and set-up steps release
+ * (per device, up to 16 GiB a process) and hands them out again for later requests of about the
+ * same size, since cudaMalloc / cudaFree cost tens to hundreds of microseconds each.  A released
+ * block is cached only after the device has finished the work queued before the release (as
+ * cudaFree would), so a cached block is never in use.  This call returns every cached block to the
+ * CUDA runtime and the number of bytes returned; a failing cudaMalloc does the same for its device
+ * before it retries. */
+size_t hec_release_cached_memory(void);
+
 /* Library version and the number of kernel launches issued by this process so far (host
  * counter, incremented by every launch the library makes). */
 int hec_version(void);

@@ -193,7 +193,7 @@ hec_status validate_csr(int n, const int* rp, const int* col, int uplo, cudaStre
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, code, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(code);
+    dfree(code);
     if (e != cudaSuccess) return cuda_error(e, "validate");
     switch (h) {
         case 0: return HEC_OK;
@@ -221,7 +221,7 @@ hec_status compute_levels(int n, const int* rp, const int* col, int dep_side, he
         HEC_CUDA(cudaMemsetAsync(lv->level, 0xFF, sizeof(int) * (size_t)n, s));
         const int threads = 256;
         int per_sm = max_coop_blocks((const void*)k_levels, threads, 0);
-        if (per_sm <= 0) { cudaFree(dnlev); return set_error(HEC_ERR_CUDA, "level kernel cannot be resident"); }
+        if (per_sm <= 0) { dfree(dnlev); return set_error(HEC_ERR_CUDA, "level kernel cannot be resident"); }
         int chunks = (n + 31) / 32;
         int blocks = std::min(per_sm * num_sms(), (chunks + threads / 32 - 1) / (threads / 32));
         blocks = std::max(blocks, 1);
@@ -234,7 +234,7 @@ hec_status compute_levels(int n, const int* rp, const int* col, int dep_side, he
     int h[2] = {0, 0};
     HEC_CUDA(cudaMemcpyAsync(h, dnlev, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     HEC_CUDA(cudaStreamSynchronize(s));
-    cudaFree(dnlev);
+    dfree(dnlev);
     if (h[1] != 0) return set_error((hec_status)h[1], "level analysis: dependency wait timed out");
     lv->nlev = h[0];
     HEC_CHECK(dalloc(&lv->level_ptr, (size_t)lv->nlev + 1));
@@ -254,7 +254,7 @@ hec_status compute_levels(int n, const int* rp, const int* col, int dep_side, he
     hec_status st = HEC_OK;
     if ((st = dalloc(&k0, (size_t)n)) || (st = dalloc(&v0, (size_t)n)) || (st = dalloc(&k1, (size_t)n)) ||
         (st = dalloc(&v1, (size_t)n)) || (st = dalloc(&counts, (size_t)kDigits * ntiles + 1))) {
-        cudaFree(k0); cudaFree(v0); cudaFree(k1); cudaFree(v1); cudaFree(counts);
+        dfree(k0); dfree(v0); dfree(k1); dfree(v1); dfree(counts);
         return st;
     }
     k_init_keys<<<(n + 255) / 256, 256, 0, s>>>(n, dep_side, lv->level, k0, v0);
@@ -281,7 +281,7 @@ hec_status compute_levels(int n, const int* rp, const int* col, int dep_side, he
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_error(e, "level sort");
     }
-    cudaFree(k0); cudaFree(v0); cudaFree(k1); cudaFree(v1); cudaFree(counts);
+    dfree(k0); dfree(v0); dfree(k1); dfree(v1); dfree(counts);
     return st;
 }
 
@@ -294,7 +294,7 @@ hec_status sort_pairs_i32(int* keys, int* vals, int n, int max_key, cudaStream_t
     hec_status st = HEC_OK;
     if ((st = dalloc(&k1, (size_t)n)) || (st = dalloc(&v1, (size_t)n)) ||
         (st = dalloc(&counts, (size_t)kDigits * ntiles + 1))) {
-        cudaFree(k1); cudaFree(v1); cudaFree(counts);
+        dfree(k1); dfree(v1); dfree(counts);
         return st;
     }
     int bits = 0;
@@ -318,16 +318,16 @@ hec_status sort_pairs_i32(int* keys, int* vals, int n, int max_key, cudaStream_t
     }
     cudaError_t e = cudaStreamSynchronize(s);
     if (st == HEC_OK && e != cudaSuccess) st = cuda_error(e, "sort");
-    cudaFree(k1); cudaFree(v1); cudaFree(counts);
+    dfree(k1); dfree(v1); dfree(counts);
     return st;
 }
 
 void free_levels(hec_levels* lv) {
     if (!lv) return;
-    cudaFree(lv->level);
-    cudaFree(lv->perm);
-    cudaFree(lv->iperm);
-    cudaFree(lv->level_ptr);
+    dfree(lv->level);
+    dfree(lv->perm);
+    dfree(lv->iperm);
+    dfree(lv->level_ptr);
     delete lv;
 }
 

@@ -170,8 +170,8 @@ HEC_API hec_status sptrsv_plan_check(const sptrsv_plan* p, void* stream) {
     unsigned* seen = nullptr;
     HEC_CHECK(dalloc(&res, 1));
     hec_status st = dalloc(&seen, (size_t)(n + 31) / 32);
-    if (st) { cudaFree(res); return st; }
-    auto finish = [&](hec_status e) { cudaFree(res); cudaFree(seen); return e; };
+    if (st) { dfree(res); return st; }
+    auto finish = [&](hec_status e) { dfree(res); dfree(seen); return e; };
     if (cudaMemsetAsync(res, 0xff, sizeof(unsigned), s) != cudaSuccess) return finish(cuda_error(cudaGetLastError(), "memset"));
     const int g = std::min(4096, (n + 255) / 256);
     k_check_levels<<<g, 256, 0, s>>>(n, lv->nlev, lv->perm, lv->iperm, lv->level_ptr, res);

@@ -1,7 +1,9 @@
 // Error reporting, allocation helpers, launch accounting and the device exclusive scan.
 #include <atomic>
 #include <cstdio>
+#include <map>
 #include <mutex>
+#include <unordered_map>
 #include <string>
 #include <utility>
 #include <vector>
@@ -28,15 +30,113 @@ hec_status cuda_error(cudaError_t e, const char* what) {
 void clear_error() { g_last_error.clear(); }
 void count_launch(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+// ---- device memory cache -------------------------------------------------------------------
+// Handles and the temporaries of set-up are allocated and released many times with the same sizes
+// (a solver built per system, a restart's workspace per solve).  cudaMalloc and cudaFree cost tens
+// to hundreds of microseconds each (cudaFree also waits for the device), so released blocks are
+// kept per device and handed out again: dfree waits for the device, as cudaFree does, and then
+// keeps the block, so a cached block is never in use by queued work.  Sizes are rounded (512 bytes
+// below 1 MiB, 1 MiB above) and a cached block is reused for a request of at least 4/5 of its
+// size.  The cache holds at most kCacheCap bytes a process; hec_release_cached_memory() and a
+// failing cudaMalloc release it.
+namespace {
+struct Block {
+    size_t size;
+    int dev;
+};
+std::mutex g_mem_mu;
+std::unordered_map<void*, Block>* g_live = new std::unordered_map<void*, Block>();      // handed out
+std::multimap<std::pair<int, size_t>, void*>* g_cache = new std::multimap<std::pair<int, size_t>, void*>();
+size_t g_cached_bytes = 0;
+constexpr size_t kCacheCap = (size_t)16 << 30;
+
+size_t round_block(size_t b) {
+    if (b == 0) b = 16;
+    if (b < ((size_t)1 << 20)) return (b + 511) & ~(size_t)511;
+    return (b + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
+}
+
+// frees cached blocks (of every device when dev < 0) until at most `keep` bytes stay; lock held
+size_t trim_cache_locked(int dev, size_t keep) {
+    size_t freed = 0;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    for (auto it = g_cache->end(); it != g_cache->begin() && g_cached_bytes > keep;) {
+        --it;
+        if (dev >= 0 && it->first.first != dev) continue;
+        if (it->first.first != cur) cudaSetDevice(it->first.first);
+        cudaFree(it->second);
+        if (it->first.first != cur) cudaSetDevice(cur);
+        g_cached_bytes -= it->first.second;
+        freed += it->first.second;
+        it = g_cache->erase(it);
+    }
+    return freed;
+}
+}  // namespace
+
 hec_status dmalloc(void** p, size_t bytes) {
     *p = nullptr;
-    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    const size_t sz = round_block(bytes);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> g(g_mem_mu);
+        auto it = g_cache->lower_bound({dev, sz});
+        if (it != g_cache->end() && it->first.first == dev && it->first.second - sz <= it->first.second / 5) {
+            *p = it->second;
+            (*g_live)[*p] = Block{it->first.second, dev};
+            g_cached_bytes -= it->first.second;
+            g_cache->erase(it);
+            return HEC_OK;
+        }
+    }
+    cudaError_t e = cudaMalloc(p, sz);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        {
+            std::lock_guard<std::mutex> g(g_mem_mu);
+            trim_cache_locked(dev, 0);
+        }
+        e = cudaMalloc(p, sz);
+    }
     if (e != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
         return cuda_error(e, "cudaMalloc");
     }
+    std::lock_guard<std::mutex> g(g_mem_mu);
+    (*g_live)[*p] = Block{sz, dev};
     return HEC_OK;
+}
+
+void dfree(void* p) {
+    if (!p) return;
+    Block b{0, -1};
+    {
+        std::lock_guard<std::mutex> g(g_mem_mu);
+        auto it = g_live->find(p);
+        if (it != g_live->end()) {
+            b = it->second;
+            g_live->erase(it);
+        }
+    }
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (b.dev < 0 || b.dev != cur) {  // not from dmalloc, or another device: release it outright
+        cudaFree(p);
+        return;
+    }
+    // queued work may still use the block: wait for the device, as cudaFree does
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p);
+        return;
+    }
+    std::lock_guard<std::mutex> g(g_mem_mu);
+    g_cache->insert({{b.dev, b.size}, p});
+    g_cached_bytes += b.size;
+    if (g_cached_bytes > kCacheCap) trim_cache_locked(-1, kCacheCap);
 }
 
 int num_sms() {
@@ -153,7 +253,7 @@ hec_status exclusive_scan_i32(const int* in, int* out, int n, bool write_total, 
     }
     // sums must outlive the kernels that read it: free after the stream drains this work
     cudaError_t e = cudaStreamSynchronize(s);
-    cudaFree(sums);
+    dfree(sums);
     if (st == HEC_OK && e != cudaSuccess) st = cuda_error(e, "scan sync");
     return st;
 }
@@ -246,3 +346,8 @@ HEC_API hec_status hec_profile_read(double* sweep_ms, long long* launches, int r
 HEC_API const char* hec_last_error(void) { return hec::g_last_error.c_str(); }
 HEC_API int hec_version(void) { return 1; }
 HEC_API long long hec_launch_count(void) { return hec::g_launches.load(); }
+
+HEC_API size_t hec_release_cached_memory(void) {
+    std::lock_guard<std::mutex> g(hec::g_mem_mu);
+    return hec::trim_cache_locked(-1, 0);
+}

@@ -857,19 +857,19 @@ namespace {
 
 void free_net(hec_net* N) {
     if (!N) return;
-    cudaFree(N->P); cudaFree(N->G); cudaFree(N->M); cudaFree(N->V); cudaFree(N->Wf); cudaFree(N->Wd); cudaFree(N->Wx);
-    for (auto& a : N->act) cudaFree(a);
-    for (auto& a : N->dA) cudaFree(a);
-    cudaFree(N->out); cudaFree(N->partial); cudaFree(N->lpart); cudaFree(N->status); cudaFree(N->words);
+    dfree(N->P); dfree(N->G); dfree(N->M); dfree(N->V); dfree(N->Wf); dfree(N->Wd); dfree(N->Wx);
+    for (auto& a : N->act) dfree(a);
+    for (auto& a : N->dA) dfree(a);
+    dfree(N->out); dfree(N->partial); dfree(N->lpart); dfree(N->status); dfree(N->words);
     delete N;
 }
 
 hec_status ensure(hec_net* N, long nvox, long nblk) {
     if (nvox > N->cap) {
-        for (auto& a : N->act) { cudaFree(a); a = nullptr; }
-        for (auto& a : N->dA) { cudaFree(a); a = nullptr; }
-        cudaFree(N->out);
-        cudaFree(N->words);
+        for (auto& a : N->act) { dfree(a); a = nullptr; }
+        for (auto& a : N->dA) { dfree(a); a = nullptr; }
+        dfree(N->out);
+        dfree(N->words);
         N->out = nullptr;
         N->words = nullptr;
         N->cap = 0;
@@ -880,7 +880,7 @@ hec_status ensure(hec_net* N, long nvox, long nblk) {
         N->cap = nvox;
     }
     if (nblk > N->partial_cap) {
-        cudaFree(N->partial);
+        dfree(N->partial);
         N->partial = nullptr;
         HEC_CHECK(dalloc(&N->partial, (size_t)nblk * PSZ));
         N->partial_cap = nblk;

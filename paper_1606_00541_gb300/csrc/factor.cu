@@ -217,9 +217,9 @@ hec_status read_code(int* dcode, cudaStream_t s, int* h) {
 
 void free_csr(hec_csr* M) {
     if (!M) return;
-    cudaFree(M->rowptr);
-    cudaFree(M->col);
-    cudaFree(M->val);
+    dfree(M->rowptr);
+    dfree(M->col);
+    dfree(M->val);
     delete M;
 }
 
@@ -281,7 +281,7 @@ HEC_API hec_status csr_triangle(int n, const int* rowptr, const int* col, const 
     int* len = nullptr;
     hec_status st = HEC_OK;
     auto fail = [&](hec_status e) {
-        cudaFree(len);
+        dfree(len);
         free_csr(T);
         return e;
     };
@@ -299,7 +299,7 @@ HEC_API hec_status csr_triangle(int n, const int* rowptr, const int* col, const 
     if (n > 0) k_tri_fill<<<g, 256, 0, s>>>(n, rowptr, col, val, uplo, strict, T->rowptr, T->col, T->val);
     count_launch();
     HEC_CUDA(cudaGetLastError());
-    cudaFree(len);
+    dfree(len);
     *out = T;
     return HEC_OK;
 }
@@ -323,9 +323,9 @@ HEC_API hec_status ilu_factor(int n, const int* rowptr, const int* col, const do
     hec_csr *L = new hec_csr(), *U = new hec_csr();
     hec_status st = HEC_OK;
     auto cleanup = [&]() {
-        cudaFree(dg); cudaFree(code); cudaFree(done); cudaFree(plen); cudaFree(lu);
-        if (prp != rowptr) cudaFree(prp);
-        if (pci != col) cudaFree(pci);
+        dfree(dg); dfree(code); dfree(done); dfree(plen); dfree(lu);
+        if (prp != rowptr) dfree(prp);
+        if (pci != col) dfree(pci);
         free_levels(lv);
     };
     auto fail = [&](hec_status e) {
@@ -407,7 +407,7 @@ HEC_API hec_status ilu_factor(int n, const int* rowptr, const int* col, const do
     // ---- split into L (unit lower, diagonal stored) and U ----
     int *llen = nullptr, *ulen = nullptr;
     if ((st = dalloc(&llen, (size_t)n + 1)) || (st = dalloc(&ulen, (size_t)n + 1))) {
-        cudaFree(llen);
+        dfree(llen);
         return fail(st);
     }
     k_split_len<<<g, 256, 0, s>>>(n, prp, dg, llen, ulen);
@@ -415,11 +415,11 @@ HEC_API hec_status ilu_factor(int n, const int* rowptr, const int* col, const do
     L->n = U->n = n;
     if ((st = dalloc(&L->rowptr, (size_t)n + 1)) || (st = dalloc(&U->rowptr, (size_t)n + 1)) ||
         (st = exclusive_scan_i32(llen, L->rowptr, n, true, s)) || (st = exclusive_scan_i32(ulen, U->rowptr, n, true, s))) {
-        cudaFree(llen); cudaFree(ulen);
+        dfree(llen); dfree(ulen);
         return fail(st);
     }
-    cudaFree(llen);
-    cudaFree(ulen);
+    dfree(llen);
+    dfree(ulen);
     int ln = 0, un = 0;
     HEC_CUDA(cudaMemcpy(&ln, L->rowptr + n, sizeof(int), cudaMemcpyDeviceToHost));
     HEC_CUDA(cudaMemcpy(&un, U->rowptr + n, sizeof(int), cudaMemcpyDeviceToHost));

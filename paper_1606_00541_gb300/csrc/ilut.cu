@@ -346,8 +346,8 @@ HEC_API hec_status ilut_factor(int n, const int* rowptr, const int* col, const d
         *url = nullptr;
     double *lval = nullptr, *uval = nullptr;
     auto cleanup = [&]() {
-        cudaFree(lcol); cudaFree(llen); cudaFree(ucol); cudaFree(ulen); cudaFree(status); cudaFree(lrl);
-        cudaFree(url); cudaFree(lval); cudaFree(uval);
+        dfree(lcol); dfree(llen); dfree(ucol); dfree(ulen); dfree(status); dfree(lrl);
+        dfree(url); dfree(lval); dfree(uval);
     };
     auto fail = [&](hec_status e) {
         cleanup();

@@ -38,8 +38,10 @@ void count_launch(long long k = 1);
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// device allocation that reports OOM as a status
+// device allocation that reports OOM as a status, and its release (common.cu: a per-device cache of
+// released blocks; dfree waits for the device before it keeps a block, as cudaFree would)
 hec_status dmalloc(void** p, size_t bytes);
+void dfree(void* p);
 template <typename T>
 hec_status dalloc(T** p, size_t count) { return dmalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16); }
 

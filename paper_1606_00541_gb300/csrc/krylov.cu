@@ -628,7 +628,7 @@ struct Dots {
         nblk = num_sms() * 2;
         return dalloc(&partial, (size_t)maxcount * nblk * K);
     }
-    ~Dots() { cudaFree(partial); }
+    ~Dots() { dfree(partial); }
     template <int KP>
     void run_kp(int n, int K, const double* V, long vstride, int count, int self, const double* w, double* out,
                 const int* gate, cudaStream_t s) {
@@ -670,7 +670,7 @@ struct Mgs {
         // MGS: two single-slot buffers; CGS: two regions of (m + 2) projections
         return dalloc(&partial, (size_t)2 * (m + 2) * cap_blocks * 16);
     }
-    ~Mgs() { cudaFree(partial); }
+    ~Mgs() { dfree(partial); }
     template <int KP>
     hec_status run_kp(int n, int K, int j, double rtol, const double* V, long vstride, double* w,
                       ArnoldiState& st, cudaStream_t s) {
@@ -939,7 +939,7 @@ HEC_API hec_status stage_create(hec_net* net, const hec_matrix* A, int nx, int n
     const long n = A->n;
     hec_status st = HEC_OK;
     auto fail = [&](hec_status e) {
-        cudaFree(S->aux); cudaFree(S->work); cudaFree(S->scal); cudaFree(S->counters); cudaFree(S->part);
+        dfree(S->aux); dfree(S->work); dfree(S->scal); dfree(S->counters); dfree(S->part);
         delete S;
         return e;
     };
@@ -974,11 +974,11 @@ HEC_API hec_status stage_stats(const hec_stage* S, int* applied, int* accepted, 
 
 HEC_API hec_status stage_destroy(hec_stage* S) {
     if (!S) return HEC_OK;
-    cudaFree(S->aux);
-    cudaFree(S->work);
-    cudaFree(S->scal);
-    cudaFree(S->counters);
-    cudaFree(S->part);
+    dfree(S->aux);
+    dfree(S->work);
+    dfree(S->scal);
+    dfree(S->counters);
+    dfree(S->part);
     delete S;
     return HEC_OK;
 }
@@ -1012,10 +1012,10 @@ struct FgmresWork {
     int* pinned = nullptr;     // host ring of per-iteration "any active" flags
     cudaEvent_t ev[2] = {nullptr, nullptr};
     ~FgmresWork() {
-        cudaFree(V);
-        cudaFree(Z);
-        cudaFree(small);
-        cudaFree(ints);
+        dfree(V);
+        dfree(Z);
+        dfree(small);
+        dfree(ints);
         if (pinned) cudaFreeHost(pinned);
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);

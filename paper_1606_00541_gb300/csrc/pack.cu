@@ -195,11 +195,11 @@ size_t vsize(hec_dtype d) { return d == HEC_F64 ? 8 : d == HEC_F32 ? 4 : 2; }
 
 void free_matrix(hec_matrix* M) {
     if (!M) return;
-    cudaFree(M->ell_col);
-    cudaFree(M->ell_val);
-    cudaFree(M->tptr);
-    cudaFree(M->tcol);
-    cudaFree(M->tval);
+    dfree(M->ell_col);
+    dfree(M->ell_val);
+    dfree(M->tptr);
+    dfree(M->tcol);
+    dfree(M->tval);
     delete M;
 }
 
@@ -229,8 +229,8 @@ HEC_API hec_status hec_from_csr(int n, const int* rowptr, const int* col, const 
     int* small = nullptr;  // [0] max count, [1] tail total
     hec_status st = HEC_OK;
     auto fail = [&](hec_status e) {
-        cudaFree(cnt);
-        cudaFree(small);
+        dfree(cnt);
+        dfree(small);
         free_matrix(M);
         return e;
     };
@@ -260,7 +260,7 @@ HEC_API hec_status hec_from_csr(int n, const int* rowptr, const int* col, const 
         std::vector<int> h((size_t)maxcnt + 1);
         cudaError_t e = cudaMemcpyAsync(h.data(), hist, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        cudaFree(hist);
+        dfree(hist);
         if (e != cudaSuccess) return fail(cuda_error(e, "hec_from_csr: histogram"));
         // largest w with #rows(count >= w) >= ceil(0.65 n)
         long long need = (long long)((65LL * n + 99) / 100);
@@ -292,8 +292,8 @@ HEC_API hec_status hec_from_csr(int n, const int* rowptr, const int* col, const 
     if (st) return fail(st);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(cuda_error(e, "hec_from_csr: pack"));
-    cudaFree(cnt);
-    cudaFree(small);
+    dfree(cnt);
+    dfree(small);
     *out = M;
     return HEC_OK;
 }
@@ -346,7 +346,7 @@ HEC_API hec_status hec_to_csr(const hec_matrix* A, const hec_levels* lv, int* ro
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_error(e, "hec_to_csr");
     }
-    cudaFree(len);
+    dfree(len);
     return st;
 }
 

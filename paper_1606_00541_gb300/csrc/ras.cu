@@ -119,9 +119,9 @@ __global__ void k_sub_rows(int n_ext, const int* __restrict__ rp, const int* __r
 
 void free_ras(hec_ras* R) {
     if (!R) return;
-    cudaFree(R->ext_ptr);
-    cudaFree(R->ext2glob);
-    cudaFree(R->owned);
+    dfree(R->ext_ptr);
+    dfree(R->ext2glob);
+    dfree(R->owned);
     free_csr(R->A_ext);
     delete R;
 }
@@ -148,8 +148,8 @@ HEC_API hec_status ras_setup_overlap(int n, const int* rowptr, const int* col, c
         *pos = nullptr, *sub = nullptr, *len = nullptr;
     hec_status st = HEC_OK;
     auto cleanup = [&]() {
-        cudaFree(code); cudaFree(cnt); cudaFree(off); cudaFree(keys); cudaFree(vals); cudaFree(flag);
-        cudaFree(pos); cudaFree(sub); cudaFree(len);
+        dfree(code); dfree(cnt); dfree(off); dfree(keys); dfree(vals); dfree(flag);
+        dfree(pos); dfree(sub); dfree(len);
     };
     auto fail = [&](hec_status e) {
         cleanup();

@@ -31,7 +31,7 @@ void free_sgs(hec_sgs* S) {
     for (auto* h : S->strict) hec_matrix_destroy(h);
     for (auto* l : S->lv) hec_levels_destroy(l);
     for (auto* t : S->tri) hec_csr_destroy(t);
-    cudaFree(S->r);
+    hec::dfree(S->r);
     delete S;
 }
 }  // namespace

@@ -1171,7 +1171,7 @@ hec_status build_chunks(sptrsv_plan* p, unsigned needed) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_error(e, "chunk table");
     }
-    cudaFree(cptr);
+    dfree(cptr);
     return st;
 }
 
@@ -1317,19 +1317,19 @@ hec_status ilu_compose(const ilu_precond* M, const hec_part_data* P, bool lower,
 
 void free_part(hec_part_data* P) {
     if (!P) return;
-    cudaFree(P->rowg); cudaFree(P->part_row); cudaFree(P->part_seg); cudaFree(P->seg_start);
-    cudaFree(P->ell_col); cudaFree(P->ell_val); cudaFree(P->tptr); cudaFree(P->tcol); cudaFree(P->tval); cudaFree(P->dinv);
-    cudaFree(P->bp); cudaFree(P->part_chunk); cudaFree(P->chunks);
-    cudaFree(P->xpb[0]); cudaFree(P->xpb[1]); cudaFree(P->pos); cudaFree(P->bidx_perm);
+    dfree(P->rowg); dfree(P->part_row); dfree(P->part_seg); dfree(P->seg_start);
+    dfree(P->ell_col); dfree(P->ell_val); dfree(P->tptr); dfree(P->tcol); dfree(P->tval); dfree(P->dinv);
+    dfree(P->bp); dfree(P->part_chunk); dfree(P->chunks);
+    dfree(P->xpb[0]); dfree(P->xpb[1]); dfree(P->pos); dfree(P->bidx_perm);
     delete P;
 }
 
 void free_plan(sptrsv_plan* p) {
     if (!p) return;
-    cudaFree(p->xp);
-    cudaFree(p->status);
-    for (int i = 0; i < 5; ++i) cudaFree(p->chunks[i]);
-    cudaFree(p->dinv);
+    dfree(p->xp);
+    dfree(p->status);
+    for (int i = 0; i < 5; ++i) dfree(p->chunks[i]);
+    dfree(p->dinv);
     free_part(p->part);
     delete p;
 }
@@ -1465,7 +1465,7 @@ hec_status build_partition(sptrsv_plan* p, const int* part, int nparts, cudaStre
     int *key = nullptr, *flag = nullptr, *segidx = nullptr, *sigma = nullptr, *len = nullptr, *bad = nullptr;
     hec_status st = HEC_OK;
     auto done = [&](hec_status e) {
-        cudaFree(key); cudaFree(flag); cudaFree(segidx); cudaFree(sigma); cudaFree(len); cudaFree(bad);
+        dfree(key); dfree(flag); dfree(segidx); dfree(sigma); dfree(len); dfree(bad);
         if (e != HEC_OK) free_part(P);
         return e;
     };
@@ -1500,19 +1500,19 @@ hec_status build_partition(sptrsv_plan* p, const int* part, int nparts, cudaStre
     {
         int* cseg = nullptr;
         if ((st = dalloc(&cseg, (size_t)P->nseg + 1)) || (st = dalloc(&P->part_chunk, (size_t)nparts + 1))) {
-            cudaFree(cseg);
+            dfree(cseg);
             return done(st);
         }
         k_chunk_counts<<<(P->nseg + 255) / 256, 256, 0, s>>>(P->nseg, P->seg_start, 32, cseg);
         count_launch();
-        if ((st = exclusive_scan_i32(cseg, cseg, P->nseg, true, s))) { cudaFree(cseg); return done(st); }
+        if ((st = exclusive_scan_i32(cseg, cseg, P->nseg, true, s))) { dfree(cseg); return done(st); }
         cudaMemcpy(&P->nchunks, cseg + P->nseg, sizeof(int), cudaMemcpyDeviceToHost);
-        if ((st = dalloc(&P->chunks, (size_t)P->nchunks))) { cudaFree(cseg); return done(st); }
+        if ((st = dalloc(&P->chunks, (size_t)P->nchunks))) { dfree(cseg); return done(st); }
         k_chunk_table<<<(P->nchunks + 255) / 256, 256, 0, s>>>(P->nseg, P->seg_start, cseg, 32, P->nchunks, P->chunks);
         k_gather_idx<<<(nparts + 256) / 256, 256, 0, s>>>(nparts + 1, P->part_seg, cseg, P->part_chunk);
         count_launch(2);
         cudaError_t ce = cudaStreamSynchronize(s);
-        cudaFree(cseg);
+        dfree(cseg);
         if (ce != cudaSuccess) return done(cuda_error(ce, "partition chunks"));
         std::vector<int> pr((size_t)nparts + 1);
         HEC_CUDA(cudaMemcpy(pr.data(), P->part_row, sizeof(int) * pr.size(), cudaMemcpyDeviceToHost));
@@ -1761,7 +1761,7 @@ HEC_API hec_status sptrsv_autotune(sptrsv_plan* p, int nrhs, hec_tune* out, void
     const size_t cnt = (size_t)std::max(T->n, 1) * nrhs;
     HEC_CHECK(dalloc(&b, cnt));
     hec_status st = dalloc(&x, cnt);
-    if (st) { cudaFree(b); return st; }
+    if (st) { dfree(b); return st; }
     cudaMemsetAsync(b, 0, sizeof(double) * cnt, s);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -1807,8 +1807,8 @@ HEC_API hec_status sptrsv_autotune(sptrsv_plan* p, int nrhs, hec_tune* out, void
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(b);
-    cudaFree(x);
+    dfree(b);
+    dfree(x);
     if (st) { apply_choice(p, saved, nullptr); return st; }
     apply_choice(p, bc, out);
     {
@@ -1868,12 +1868,12 @@ HEC_API hec_status ilu_create(const sptrsv_plan* L, const sptrsv_plan* U, int n_
 
 HEC_API hec_status ilu_destroy(ilu_precond* M) {
     if (!M) return HEC_OK;
-    cudaFree(M->l_gather);
-    cudaFree(M->l_scatter);
-    cudaFree(M->u_scatter);
-    cudaFree(M->y);
-    cudaFree(M->lg_part);
-    cudaFree(M->ls_upart);
+    dfree(M->l_gather);
+    dfree(M->l_scatter);
+    dfree(M->u_scatter);
+    dfree(M->y);
+    dfree(M->lg_part);
+    dfree(M->ls_upart);
     delete M;
     return HEC_OK;
 }

@@ -166,6 +166,15 @@ def library_path():
     return LIB_PATH
 
 
+_lib.hec_release_cached_memory.restype = ctypes.c_size_t
+
+
+def release_cached_memory():
+    """Returns the device blocks the library keeps for reuse to the CUDA runtime; the number of
+    bytes returned (hec_release_cached_memory)."""
+    return int(_lib.hec_release_cached_memory())
+
+
 GS_CLASSICAL, GS_MODIFIED = 0, 1
 _hec_set_gram_schmidt = _sig("hec_set_gram_schmidt", _i)
 
