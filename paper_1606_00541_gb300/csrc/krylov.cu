@@ -83,6 +83,62 @@ __global__ void __launch_bounds__(kThreads) k_spmv(int n, int ld, int w, const i
     }
 }
 
+// y = alpha A x + beta y for one right-hand side, persistent: a grid of resident blocks, each
+// thread takes rows r, r + (threads of the grid), ... and loads the next row's slab and tail range
+// while its current row's x gathers are in flight, so a thread keeps the loads of two rows
+// outstanding instead of waiting on one row's column loads, then its gathers, in turn.  The
+// per-row arithmetic is k_spmv's (slab slots in order, then the tail), so the results are the same
+// bit for bit.
+template <int WMAX>
+__global__ void __launch_bounds__(kThreads) k_spmv1(int n, int ld, int w, const int* __restrict__ ell_col,
+                                                    const double* __restrict__ ell_val, const int* __restrict__ tptr,
+                                                    const int* __restrict__ tcol, const double* __restrict__ tval,
+                                                    double alpha, const double* __restrict__ x, double beta,
+                                                    double* __restrict__ y) {
+    const long st = (long)gridDim.x * blockDim.x;
+    long r = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    int c[WMAX], t0 = 0, t1 = 0;
+    double v[WMAX];
+    auto load = [&](long rr) {
+#pragma unroll
+        for (int k = 0; k < WMAX; ++k) {
+            c[k] = -1;
+            v[k] = 0.0;
+            if (k < w && rr < n) {
+                c[k] = __ldg(ell_col + (long)k * ld + rr);
+                v[k] = __ldg(ell_val + (long)k * ld + rr);
+            }
+        }
+        if (rr < n) {
+            t0 = __ldg(tptr + rr);
+            t1 = __ldg(tptr + rr + 1);
+        }
+    };
+    load(r);
+    while (r < n) {
+        int cc[WMAX];
+        double vv[WMAX];
+#pragma unroll
+        for (int k = 0; k < WMAX; ++k) {
+            cc[k] = c[k];
+            vv[k] = v[k];
+        }
+        const int a0 = t0, a1 = t1;
+        const long rn = r + st;
+        load(rn);
+        double xs[WMAX];
+#pragma unroll
+        for (int k = 0; k < WMAX; ++k) xs[k] = cc[k] >= 0 ? __ldg(x + cc[k]) : 0.0;
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < WMAX; ++k)
+            if (cc[k] >= 0) acc = fma(vv[k], xs[k], acc);
+        for (int t = a0; t < a1; ++t) acc = fma(__ldg(tval + t), __ldg(x + __ldg(tcol + t)), acc);
+        y[r] = beta == 0.0 ? (alpha == 1.0 ? acc : alpha * acc) : fma(beta, y[r], alpha * acc);
+        r = rn;
+    }
+}
+
 // dst (dense n x K) = src (n x K with leading dimension lds)
 __global__ void k_copy(long total, int K, const double* __restrict__ src, int lds, double* __restrict__ dst, int ldd) {
     long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -717,6 +773,25 @@ struct Mgs {
 hec_status spmv_impl(const hec_matrix* A, int K, double alpha, const double* x, int ldx, double beta, double* y,
                      int ldy, cudaStream_t s) {
     if (A->n == 0) return HEC_OK;
+    if (K == 1 && ldx == 1 && ldy == 1 && A->w <= 8) {
+        const void* k = A->w <= 4 ? (const void*)k_spmv1<4> : (const void*)k_spmv1<8>;
+        static int per_sm[2] = {-1, -1};
+        int& ps = per_sm[A->w <= 4 ? 0 : 1];
+        if (ps < 0) ps = max_coop_blocks(k, kThreads, 0);
+        const long want = ((long)A->n + kThreads - 1) / kThreads;
+        const int blocks = (int)std::max(1L, std::min<long>((long)std::max(ps, 1) * num_sms(), want));
+        {
+            ProfScope ps_(s, PROF_SPMV);
+            if (A->w <= 4)
+                k_spmv1<4><<<blocks, kThreads, 0, s>>>(A->n, A->ld, A->w, A->ell_col, (const double*)A->ell_val, A->tptr,
+                                                      A->tcol, (const double*)A->tval, alpha, x, beta, y);
+            else
+                k_spmv1<8><<<blocks, kThreads, 0, s>>>(A->n, A->ld, A->w, A->ell_col, (const double*)A->ell_val, A->tptr,
+                                                      A->tcol, (const double*)A->tval, alpha, x, beta, y);
+        }
+        HEC_LAUNCHED();
+        return HEC_OK;
+    }
     auto go = [&](auto kp) -> hec_status {
         constexpr int KP = decltype(kp)::value;
         constexpr int RPT = KP == 1 ? 2 : 1;
