@@ -412,7 +412,7 @@ hec_status stage_stats(const hec_stage* stage, int* applied, int* accepted, int 
 hec_status stage_destroy(hec_stage* stage);
 
 /* ---------------------------------------------------------------------------------------- */
-/* Incomplete factorizations on the GPU (Sec. 3): ILU(0) and ILU(1) of a CSR matrix            */
+/* Incomplete factorizations on the GPU (Sec. 3): ILU(k) and ILUT of a CSR matrix               */
 /* ---------------------------------------------------------------------------------------- */
 
 /* Device CSR owned by the library. */
@@ -448,13 +448,18 @@ hec_status sgs_smooth(const hec_sgs* sgs, int nrhs, const double* b, int ldb, do
 hec_status sgs_sync_status(const hec_sgs* sgs, void* stream);
 hec_status sgs_destroy(hec_sgs* sgs);
 
-/* ILU(k) for k = 0 (pattern of A) or k = 1 (pattern of A plus the fill of level 1: entries
- * (i, j) reached by i -> q -> j with q < min(i, j) both original entries).  Each row i is
+/* ILU(k), k >= 0 ("k is the fill-in level", Sec. 3).  The pattern: entries of A have level 0;
+ * eliminating pivot q of row i (q < i, ascending, fill pivots included) gives (i, j), j > q in U
+ * row q, the level lev(i, q) + lev(q, j) + 1, an entry keeps the smallest level it receives, and
+ * entries with level <= k are kept.  k = 0 is the pattern of A; k = 1 is built by a merge of the
+ * original rows (at most 63 pivots a row); k >= 2 by a row-dependent symbolic pass (one warp per
+ * row, a row's list capped at 4096 entries: OUT_OF_BOUNDS beyond).  Each row i is then
  * eliminated IKJ-style: for the pattern columns q < i in ascending order,
  * a_iq <- a_iq / u_qq, then a_ij <- a_ij - a_iq u_qj for pattern columns j > q of both rows.
  * Rows run in the level order of the lower pattern with point-to-point completion waits.
  * Outputs L (unit lower, the 1.0 diagonal stored) and U (upper with its diagonal).  A must have
- * a nonzero diagonal in every row; ZERO_PIVOT if an eliminated pivot is zero.  Synchronizes. */
+ * a nonzero diagonal in every row; ZERO_PIVOT if an eliminated pivot is zero; TIMEOUT if a
+ * dependency wait runs out.  Synchronizes. */
 hec_status ilu_factor(int n, const int* rowptr, const int* col, const double* val, int k,
                       hec_csr** L, hec_csr** U, void* stream);
 

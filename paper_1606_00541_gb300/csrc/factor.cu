@@ -1,4 +1,5 @@
-// Incomplete LU factorization on the GPU: ILU(0) and ILU(1) (Sec. 3).
+// Incomplete LU factorization on the GPU: ILU(0), ILU(1) and ILU(k) (Sec. 3); the ILU(k) pattern for
+// k >= 2 comes from iluk.cu.
 //
 // Row i of the factors needs the finished U rows of every q < i in its lower pattern, which is
 // the same dependency structure as the triangular solve with L.  The numeric kernel therefore
@@ -17,6 +18,8 @@
 
 namespace hec {
 hec_status validate_csr(int n, const int* rp, const int* col, int uplo, cudaStream_t s);
+hec_status iluk_pattern(int n, const int* rp, const int* ci, int k, int** prp, int** pci, long long* nnz,
+                        cudaStream_t s);
 hec_status compute_levels(int n, const int* rp, const int* col, int dep_side, hec_levels* lv, cudaStream_t s);
 void free_levels(hec_levels* lv);
 
@@ -312,8 +315,8 @@ HEC_API hec_status hec_csr_destroy(hec_csr* M) {
 HEC_API hec_status ilu_factor(int n, const int* rowptr, const int* col, const double* val, int k, hec_csr** Lout,
                               hec_csr** Uout, void* stream) {
     clear_error();
-    if (!Lout || !Uout || n < 0 || (k != 0 && k != 1) || (n > 0 && (!rowptr || !col || !val)))
-        return set_error(HEC_ERR_INVALID_ARG, "ilu_factor: bad argument (k must be 0 or 1)");
+    if (!Lout || !Uout || n < 0 || k < 0 || (n > 0 && (!rowptr || !col || !val)))
+        return set_error(HEC_ERR_INVALID_ARG, "ilu_factor: bad argument (k must be >= 0)");
     *Lout = *Uout = nullptr;
     cudaStream_t s = S(stream);
     HEC_CHECK(validate_csr(n, rowptr, col, -1, s));
@@ -348,6 +351,13 @@ HEC_API hec_status ilu_factor(int n, const int* rowptr, const int* col, const do
         pnnz = h;
         if ((st = dalloc(&lu, (size_t)pnnz))) return fail(st);
         HEC_CUDA(cudaMemcpyAsync(lu, val, sizeof(double) * (size_t)pnnz, cudaMemcpyDeviceToDevice, s));
+    } else if (k >= 2) {
+        if (n > 0) {
+            if ((st = iluk_pattern(n, rowptr, col, k, &prp, &pci, &pnnz, s))) return fail(st);
+            if ((st = dalloc(&lu, (size_t)pnnz))) return fail(st);
+            k_scatter_vals<<<g, 256, 0, s>>>(n, rowptr, col, val, prp, pci, lu);
+            count_launch();
+        }
     } else {
         if ((st = dalloc(&plen, (size_t)n + 1)) || (st = dalloc(&prp, (size_t)n + 1))) return fail(st);
         if (n > 0) {

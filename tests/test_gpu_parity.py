@@ -318,14 +318,44 @@ def test_fgmres_multi_rhs(hec):
 
 # --- GPU factorization ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("k", [0, 1])
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
 @pytest.mark.parametrize("maker", ["5pt", "fv7", "27pt", "rand"])
 def test_ilu_factor_parity(hec, k, maker):
     A = {"5pt": lambda: synth.poisson2d_5pt(40, 23), "fv7": lambda: synth.fv7_lognormal(11, seed=3),
          "27pt": lambda: synth.stencil27_jitter(7, seed=3), "rand": lambda: synth.random_sparse(600, 0.01, 8)}[maker]()
     Lh, Uh = hec.ilu_factor(*dev(A), k=k)
     L, U = [tuple(a.cpu().numpy() for a in h.tensors()) for h in (Lh, Uh)]
-    Lo, Uo = oracle.ilu0(A) if k == 0 else oracle.iluk(A, 1)
+    Lo, Uo = oracle.ilu0(A) if k == 0 else oracle.iluk(A, k)
     for got, exp in [(L, Lo), (U, Uo)]:
         assert np.array_equal(got[0], exp[0]) and np.array_equal(got[1], exp[1])
         assert relmax(got[2], exp[2]) <= 1e-12
+
+
+def test_iluk_large_k_is_exact_lu(hec):
+    """With k at least the matrix order every fill entry is kept: the GPU ILU(k) is the exact LU
+    (no pivoting) of a diagonally dominant matrix, so L U reproduces A."""
+    A = synth.random_sparse(120, 0.05, 5)
+    n = len(A[0]) - 1
+    Lh, Uh = hec.ilu_factor(*dev(A), k=n)
+    L, U = [tuple(a.cpu().numpy() for a in h.tensors()) for h in (Lh, Uh)]
+    Ld, Ud, Ad = np.zeros((n, n)), np.zeros((n, n)), np.zeros((n, n))
+    for M, (rp, ci, v) in [(Ld, L), (Ud, U), (Ad, A)]:
+        for i in range(n):
+            M[i, ci[rp[i]:rp[i + 1]]] = v[rp[i]:rp[i + 1]]
+    assert np.max(np.abs(Ld @ Ud - Ad)) <= 1e-12 * np.max(np.abs(Ad))
+
+
+def test_iluk_fgmres_with_gpu_factors(hec):
+    """GPU ILU(2) factors in the solver: FGMRES reaches the bound and the oracle's iteration count
+    with the oracle's ILU(2)."""
+    A = synth.fv7_lognormal(16, seed=7)
+    n = len(A[0]) - 1
+    Ad = dev(A)
+    Lh, Uh = hec.ilu_factor(*Ad, k=2)
+    s = hec.IluSolver(Lh.tensors(), Uh.tensors(), A=Ad, vdt="f64")
+    b = oracle.spmv(A, synth.uniform_vector(n, 9))
+    x, info = s.solve(torch.as_tensor(b, device="cuda"), rtol=1e-8, max_iters=1000)
+    assert info["converged"]
+    assert np.linalg.norm(b - oracle.spmv(A, x.cpu().numpy())) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-6)
+    ref = oracle.fgmres(A, b, ("ilu", *oracle.iluk(A, 2)), m=30, rtol=1e-8)
+    assert abs(info["iterations"] - ref["iters"]) <= 2
