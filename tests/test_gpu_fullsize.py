@@ -89,6 +89,31 @@ def test_cfg1_fgmres_fp32_factors(hec, cfg1):
     assert relmax(zg, z) <= 1e-5  # FP32 factor values: one apply within FP32-level error
 
 
+def test_cfg1_fgmres_fp64_factors_against_oracle(hec, cfg1):
+    """The solve the bench times, with FP64 factors so that the oracle runs the same method: the
+    x-pencil partitioned sweeps and classical Gram-Schmidt (the library default) against the
+    oracle's serial FGMRES(30) with modified Gram-Schmidt on the same factors.  Both reach the true
+    residual bound; the iteration counts agree within 2; the solutions agree within the
+    conditioning (1e-4)."""
+    m, A, L, U = cfg1
+    n = m ** 3
+    b = oracle.spmv(A, synth.uniform_vector(n, 1))
+    part, nparts = synth.grid_boxes(m, (1, 12, 12))
+    s = hec.IluSolver([dev(a) for a in L], [dev(a) for a in U], A=[dev(a) for a in A], vdt="f64")
+    s.partition(dev(part), nparts, threads=1024)
+    assert hec.get_gram_schmidt() == "classical"
+    x, info = s.solve(dev(b), restart=30, rtol=1e-8, max_iters=5000)
+    x = x.cpu().numpy()
+    assert info["converged"]
+    assert np.linalg.norm(b - oracle.spmv(A, x)) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-6)
+    ref = oracle.fgmres(A, b, ("ilu", L, U), m=30, rtol=1e-8, max_iters=5000)
+    assert ref["converged"]
+    assert abs(info["iterations"] - ref["iters"]) <= 2, (info["iterations"], ref["iters"])
+    assert relmax(x, ref["x"]) <= 1e-4
+    print("cfg1 FP64 factors: GPU %d iterations (%d with a second Gram-Schmidt pass), oracle %d"
+          % (info["iterations"], info["reorthogonalized"], ref["iters"]))
+
+
 @pytest.mark.parametrize("vdt", ["f32", "bf16"])
 def test_cfg1_timed_partitioned_sweeps_against_oracle(hec, cfg1, vdt):
     """The exact form bench.py times: FP32 (and BF16) factor values, the single-right-hand-side
