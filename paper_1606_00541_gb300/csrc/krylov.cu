@@ -88,9 +88,12 @@ __global__ void __launch_bounds__(kThreads) k_spmv(int n, int ld, int w, const i
 // while its current row's x gathers are in flight, so a thread keeps the loads of two rows
 // outstanding instead of waiting on one row's column loads, then its gathers, in turn.  The
 // per-row arithmetic is k_spmv's (slab slots in order, then the tail), so the results are the same
-// bit for bit.
-template <int WMAX>
-__global__ void __launch_bounds__(kThreads) k_spmv1(int n, int ld, int w, const int* __restrict__ ell_col,
+// bit for bit.  GB300's FP64 unit spends 16 SM-cycles on a warp's FP64 instruction whether its
+// lanes are on or off, so the kernel is instantiated for the exact slab width WMAX (no FMA issued
+// for slots beyond it) and the final scaling is chosen by the template MODE (0: y = Ax,
+// 1: y = alpha Ax, 2: y = alpha Ax + beta y) rather than by predicated arithmetic.
+template <int WMAX, int MODE>
+__global__ void __launch_bounds__(kThreads, 4) k_spmv1(int n, int ld, int w, const int* __restrict__ ell_col,
                                                     const double* __restrict__ ell_val, const int* __restrict__ tptr,
                                                     const int* __restrict__ tcol, const double* __restrict__ tval,
                                                     double alpha, const double* __restrict__ x, double beta,
@@ -134,7 +137,9 @@ __global__ void __launch_bounds__(kThreads) k_spmv1(int n, int ld, int w, const 
         for (int k = 0; k < WMAX; ++k)
             if (cc[k] >= 0) acc = fma(vv[k], xs[k], acc);
         for (int t = a0; t < a1; ++t) acc = fma(__ldg(tval + t), __ldg(x + __ldg(tcol + t)), acc);
-        y[r] = beta == 0.0 ? (alpha == 1.0 ? acc : alpha * acc) : fma(beta, y[r], alpha * acc);
+        if (MODE == 0) y[r] = acc;
+        else if (MODE == 1) y[r] = alpha * acc;
+        else y[r] = fma(beta, y[r], alpha * acc);
         r = rn;
     }
 }
@@ -774,23 +779,39 @@ hec_status spmv_impl(const hec_matrix* A, int K, double alpha, const double* x, 
                      int ldy, cudaStream_t s) {
     if (A->n == 0) return HEC_OK;
     if (K == 1 && ldx == 1 && ldy == 1 && A->w <= 8) {
-        const void* k = A->w <= 4 ? (const void*)k_spmv1<4> : (const void*)k_spmv1<8>;
-        static int per_sm[2] = {-1, -1};
-        int& ps = per_sm[A->w <= 4 ? 0 : 1];
-        if (ps < 0) ps = max_coop_blocks(k, kThreads, 0);
-        const long want = ((long)A->n + kThreads - 1) / kThreads;
-        const int blocks = (int)std::max(1L, std::min<long>((long)std::max(ps, 1) * num_sms(), want));
-        {
-            ProfScope ps_(s, PROF_SPMV);
-            if (A->w <= 4)
-                k_spmv1<4><<<blocks, kThreads, 0, s>>>(A->n, A->ld, A->w, A->ell_col, (const double*)A->ell_val, A->tptr,
-                                                      A->tcol, (const double*)A->tval, alpha, x, beta, y);
-            else
-                k_spmv1<8><<<blocks, kThreads, 0, s>>>(A->n, A->ld, A->w, A->ell_col, (const double*)A->ell_val, A->tptr,
-                                                      A->tcol, (const double*)A->tval, alpha, x, beta, y);
+        const int mode = beta == 0.0 ? (alpha == 1.0 ? 0 : 1) : 2;
+        auto go1 = [&](auto wm, auto md) -> hec_status {
+            constexpr int WM = decltype(wm)::value, MD = decltype(md)::value;
+            const void* k = (const void*)k_spmv1<WM, MD>;
+            static int per_sm = -1;  // per template instance
+            if (per_sm < 0) per_sm = max_coop_blocks(k, kThreads, 0);
+            const long want = ((long)A->n + kThreads - 1) / kThreads;
+            const int blocks = (int)std::max(1L, std::min<long>((long)std::max(per_sm, 1) * num_sms(), want));
+            {
+                ProfScope ps_(s, PROF_SPMV);
+                k_spmv1<WM, MD><<<blocks, kThreads, 0, s>>>(A->n, A->ld, A->w, A->ell_col, (const double*)A->ell_val,
+                                                            A->tptr, A->tcol, (const double*)A->tval, alpha, x, beta, y);
+            }
+            HEC_LAUNCHED();
+            return HEC_OK;
+        };
+        auto by_mode = [&](auto wm) -> hec_status {
+            using M0 = std::integral_constant<int, 0>;
+            using M1 = std::integral_constant<int, 1>;
+            using M2 = std::integral_constant<int, 2>;
+            return mode == 0 ? go1(wm, M0()) : mode == 1 ? go1(wm, M1()) : go1(wm, M2());
+        };
+        switch (A->w) {
+            case 0:
+            case 1: return by_mode(std::integral_constant<int, 1>());
+            case 2: return by_mode(std::integral_constant<int, 2>());
+            case 3: return by_mode(std::integral_constant<int, 3>());
+            case 4: return by_mode(std::integral_constant<int, 4>());
+            case 5: return by_mode(std::integral_constant<int, 5>());
+            case 6: return by_mode(std::integral_constant<int, 6>());
+            case 7: return by_mode(std::integral_constant<int, 7>());
+            default: return by_mode(std::integral_constant<int, 8>());
         }
-        HEC_LAUNCHED();
-        return HEC_OK;
     }
     auto go = [&](auto kp) -> hec_status {
         constexpr int KP = decltype(kp)::value;
