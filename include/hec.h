@@ -322,7 +322,9 @@ int hec_get_gram_schmidt(void);
  * device.  Inside a restart cycle the host only reads a per-iteration "still active" flag through
  * pinned memory one iteration behind the device (an event wait, the device never idles for the
  * host); `stream` is synchronized at each restart (true residual, status of the sweeps) and at
- * exit.  Allocates its workspace (restart + 1 + restart vectors of n x nrhs) per call.  Returns
+ * exit.  Allocates its workspace (restart + 1 + restart vectors of n x nrhs) per call, from the
+ * library's device memory cache; the pinned flag pair and its two events are kept per calling
+ * thread and device and reused by later calls.  Returns
  * HEC_ERR_NOT_CONVERGED when max_iters is reached, HEC_ERR_TIMEOUT when a sweep's dependency
  * wait timed out. */
 typedef struct hec_stage hec_stage;

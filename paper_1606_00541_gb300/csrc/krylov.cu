@@ -1105,18 +1105,43 @@ struct FgmresWork {
     double* Z = nullptr;       // m blocks of n x K
     double* small = nullptr;   // Arnoldi arrays
     int* ints = nullptr;
-    int* pinned = nullptr;     // host ring of per-iteration "any active" flags
-    cudaEvent_t ev[2] = {nullptr, nullptr};
     ~FgmresWork() {
         dfree(V);
         dfree(Z);
         dfree(small);
         dfree(ints);
+    }
+};
+// Host-side objects of fgmres_solve, kept per thread for the device they were made on: the pinned
+// pair of per-iteration "any active" flags and the two events that order their reads
+// (cudaHostAlloc / cudaFreeHost cost more than the rest of a solve's host work).
+struct FgmresHost {
+    int dev = -1;
+    int* pinned = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    ~FgmresHost() { release(); }
+    void release() {
         if (pinned) cudaFreeHost(pinned);
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
+        pinned = nullptr;
+        ev[0] = ev[1] = nullptr;
+        dev = -1;
+        cudaGetLastError();
+    }
+    hec_status get() {
+        int d = 0;
+        HEC_CUDA(cudaGetDevice(&d));
+        if (d == dev && pinned) return HEC_OK;
+        release();
+        HEC_CUDA(cudaHostAlloc((void**)&pinned, 2 * sizeof(int), cudaHostAllocDefault));
+        HEC_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+        HEC_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+        dev = d;
+        return HEC_OK;
     }
 };
+thread_local FgmresHost t_fgmres_host;
 }  // namespace
 
 HEC_API hec_status fgmres_solve(const hec_matrix* A, const ilu_precond* M, const hec_stage* extra, int nrhs,
@@ -1146,9 +1171,8 @@ HEC_API hec_status fgmres_solve(const hec_matrix* A, const ilu_precond* M, const
         (st = dalloc(&W.small, nsmall)) || (st = dalloc(&W.ints, (size_t)2 * K + 2)) || (st = dots.init(m + 2, K)) ||
         (st = mgs.init(m, g_gs_mode)))
         return st;
-    HEC_CUDA(cudaHostAlloc((void**)&W.pinned, 2 * sizeof(int), cudaHostAllocDefault));
-    HEC_CUDA(cudaEventCreateWithFlags(&W.ev[0], cudaEventDisableTiming));
-    HEC_CUDA(cudaEventCreateWithFlags(&W.ev[1], cudaEventDisableTiming));
+    FgmresHost& H = t_fgmres_host;
+    HEC_CHECK(H.get());
     ArnoldiState as;
     {
         double* p = W.small;
@@ -1245,13 +1269,13 @@ HEC_API hec_status fgmres_solve(const hec_matrix* A, const ilu_precond* M, const
             if (!extra || extra->A != A) HEC_CHECK(spmv_impl(A, K, 1.0, zj, K, 0.0, wv, K, s));
             // Gram-Schmidt, ||w||, Hessenberg column, rotations, w /= h_{j+1,j}
             HEC_CHECK(mgs.run(n, K, j, rtol, W.V, nk, wv, as, s));
-            HEC_CUDA(cudaMemcpyAsync(W.pinned + (j & 1), as.any, sizeof(int), cudaMemcpyDeviceToHost, s));
-            HEC_CUDA(cudaEventRecord(W.ev[j & 1], s));
+            HEC_CUDA(cudaMemcpyAsync(H.pinned + (j & 1), as.any, sizeof(int), cudaMemcpyDeviceToHost, s));
+            HEC_CUDA(cudaEventRecord(H.ev[j & 1], s));
             launched = j + 1;
             // stay at most one iteration ahead: look at the previous iteration's flag
             if (j >= 1) {
-                HEC_CUDA(cudaEventSynchronize(W.ev[(j - 1) & 1]));
-                if (W.pinned[(j - 1) & 1] == 0) break;  // every right-hand side finished at j-1
+                HEC_CUDA(cudaEventSynchronize(H.ev[(j - 1) & 1]));
+                if (H.pinned[(j - 1) & 1] == 0) break;  // every right-hand side finished at j-1
             }
         }
         // y = R^-1 g, x += Z y
