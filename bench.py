@@ -5,7 +5,7 @@ One step = one pass of the whole hot path over the workload: level analysis of L
 HEC packing of L, U and A (Sec. 2.1, Alg. 1), solve plans, and an ILU(0)-preconditioned FGMRES(30)
 solve of A x = b to a 1e-8 relative residual (FP32 factor values, FP64 outer loop), whose every
 inner iteration runs the lower and upper sweeps (Alg. 2), SpMV and the Gram-Schmidt kernels.  The
-sweeps run partitioned by default (`--sweep part`: 144 x-pencils of the grid, one 1024-thread block
+sweeps run partitioned by default (`--sweep part`: 256 x-pencils of the grid, one 512-thread block
 each, same results up to summation order); `--sweep global` times the global level-ordered kernel.  The
 ILU(0) factors are computed once on the GPU before timing.  Inputs are seeded and synthetic
 (ln k ~ N(0, 2^2), b = A x_true with x_true ~ U[-1, 1]); the working set (~1 GB) is larger than L2.
@@ -342,7 +342,7 @@ def main():
                 "avg_sweep_us": avg_launch_s * 1e6, "bytes_per_sweep": per_sweep}
     if args.sweep == "part":
         # the second bound: the dependency chain at the schedule's own measured hop latencies
-        lf = level_floor(hec, torch, devn, s.lvL.nlev, sum(k - 1 for k in sweep_grid(m)), PART_THREADS)
+        lf = level_floor(hec, torch, devn, s.lvL.nlev, sum(k - 1 for k in sweep_grid(m)), part_threads(m))
         lf["frac"] = lf["floor_us"] / (avg_launch_s * 1e6)
         roofline["latency_floor"] = lf
 
@@ -586,7 +586,6 @@ def learned_variant(hec, torch, m, seed=0, crop=32, crops=125, epochs=8, log=Non
     return res
 
 
-PART_THREADS = 1024
 
 
 class Schedule:
@@ -602,14 +601,14 @@ class Schedule:
 
     def apply(self, s, vdt="f32"):
         if self.kind == "part":
-            s.partition(self.part, self.nparts, threads=PART_THREADS)
+            s.partition(self.part, self.nparts, threads=part_threads(self.m))
 
     def kernel(self):
         return {"global": "k_sweep<float,float,1,4>", "part": "k_sweep_part<float,float,4>"}[self.kind]
 
     def describe(self):
         if self.kind == "part":
-            return "x-pencil partitioned: %d parts, %d threads per part" % (self.nparts, PART_THREADS)
+            return "x-pencil partitioned: %d parts, %d threads per part" % (self.nparts, part_threads(self.m))
         return "global level-ordered"
 
 
@@ -663,12 +662,19 @@ def level_floor(hec, torch, device, levels, crossings, threads, vdt="f32", n=409
 
 
 def sweep_grid(m):
-    """Boxes per axis of the x-pencil partition used on an m^3 grid: the y-z plane cut into 12 x 12
-    boxes (144 parts, one resident 1024-thread block each), so a dependency chain crosses a part
-    boundary at most 22 times and every other step stays in one SM's shared memory.  Grids above
-    160^3 take 8 x 19 pencils (152 parts) so that a part's FP32 solution still fits in shared
-    memory."""
-    return (1, 12, 12) if m <= 160 else (1, 8, 19)
+    """Boxes per axis of the x-pencil partition used on an m^3 grid: the y-z plane cut into 16 x 16
+    boxes (256 parts, two resident 512-thread blocks an SM), so a dependency chain crosses a part
+    boundary at most 30 times and every other step stays in one SM's shared memory.  Measured at
+    128^3, FP32 ILU(0) apply: 403 us against 432-436 us for 12 x 12 pencils of 1024 threads, 417 us
+    for 8 x 19, 432 us for 8 x 38 and 445 us for 16 x 16 with 256 threads.  Grids above 160^3
+    take 8 x 19 pencils (152 parts, one 1024-thread block each) so that a part's FP32 solution
+    still fits in shared memory."""
+    return (1, 16, 16) if m <= 160 else (1, 8, 19)
+
+
+def part_threads(m):
+    """Threads of a part's block for the partition of sweep_grid(m)."""
+    return 512 if m <= 160 else 1024
 
 
 def ras_cuts(m):

@@ -28,13 +28,17 @@ def test_sweep_bytes_match_the_printed_totals():
 
 def test_sweep_grid_parts_fit():
     from paper_1606_00541_gb300 import synth
-    for m, parts, crossings in ((128, 144, 22), (200, 152, 25)):
+    for m, parts, crossings, threads in ((128, 256, 30, 512), (200, 152, 25, 1024)):
         nb = bench.sweep_grid(m)
         part, nparts = synth.grid_boxes(m, nb)
         assert nparts == parts and sum(k - 1 for k in nb) == crossings
-        # every part is an x-pencil whose FP32 solution fits the 227 KB of shared memory a block has
+        assert bench.part_threads(m) == threads
+        # every part is an x-pencil whose FP32 solution fits the shared memory of its block: 227 KB
+        # for one 1024-thread block an SM, half of the SM's 228 KB for two 512-thread blocks
         sizes = np.bincount(part, minlength=nparts)
-        assert sizes.min() > 0 and sizes.max() * 4 <= 227 * 1024
+        per_sm = 1 if threads == 1024 else 2
+        assert sizes.min() > 0 and sizes.max() * 4 * per_sm <= 228 * 1024 - 1024 * per_sm
+        assert nparts <= 152 * per_sm
         g = np.arange(m ** 3)
         y, z = (g // m) % m, g // (m * m)
         assert np.all(part == (y * nb[1]) // m + nb[1] * ((z * nb[2]) // m))

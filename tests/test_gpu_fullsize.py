@@ -98,9 +98,9 @@ def test_cfg1_fgmres_fp64_factors_against_oracle(hec, cfg1):
     m, A, L, U = cfg1
     n = m ** 3
     b = oracle.spmv(A, synth.uniform_vector(n, 1))
-    part, nparts = synth.grid_boxes(m, (1, 12, 12))
+    part, nparts = synth.grid_boxes(m, (1, 16, 16))
     s = hec.IluSolver([dev(a) for a in L], [dev(a) for a in U], A=[dev(a) for a in A], vdt="f64")
-    s.partition(dev(part), nparts, threads=1024)
+    s.partition(dev(part), nparts, threads=512)
     assert hec.get_gram_schmidt() == "classical"
     x, info = s.solve(dev(b), restart=30, rtol=1e-8, max_iters=5000)
     x = x.cpu().numpy()
@@ -117,7 +117,7 @@ def test_cfg1_fgmres_fp64_factors_against_oracle(hec, cfg1):
 @pytest.mark.parametrize("vdt", ["f32", "bf16"])
 def test_cfg1_timed_partitioned_sweeps_against_oracle(hec, cfg1, vdt):
     """The exact form bench.py times: FP32 (and BF16) factor values, the single-right-hand-side
-    partitioned kernel on 144 x-pencils of the 128^3 grid with one 1024-thread block each.  The
+    partitioned kernel on 256 x-pencils of the 128^3 grid with one 512-thread block each.  The
     lower and upper sweeps and the ILU apply are compared element by element with the oracle's
     FP64 substitution on the same rounded values, under the componentwise FP32 bound
     gamma_{q+2}(u32) M(T)^-1 |T| |x| with a safety factor of 4; the error against the unrounded
@@ -125,8 +125,8 @@ def test_cfg1_timed_partitioned_sweeps_against_oracle(hec, cfg1, vdt):
     to 1e-12, tested above), so no input of the reference comes from the GPU."""
     m, A, L, U = cfg1
     n = m ** 3
-    part, nparts = synth.grid_boxes(m, (1, 12, 12))
-    assert nparts == 144
+    part, nparts = synth.grid_boxes(m, (1, 16, 16))
+    assert nparts == 256
     b = synth.uniform_vector(n, 1)
     xs = {}
     for uplo, T in [(0, L), (1, U)]:
@@ -134,7 +134,7 @@ def test_cfg1_timed_partitioned_sweeps_against_oracle(hec, cfg1, vdt):
         lv = hec.sptrsv_analyze(Td[0], Td[1], uplo)
         H = hec.hec_from_csr(*Td, levels=lv, vdt=vdt)
         p = hec.sptrsv_plan_create(H, lv, 1)
-        hec.sptrsv_plan_partition(p, dev(part), nparts, 1024)
+        hec.sptrsv_plan_partition(p, dev(part), nparts, 512)
         f = hec.sptrsv_lower if uplo == 0 else hec.sptrsv_upper
         x = f(p, dev(b)).cpu().numpy()
         assert hec.hec_sync_status(p) == 0
@@ -150,7 +150,7 @@ def test_cfg1_timed_partitioned_sweeps_against_oracle(hec, cfg1, vdt):
     # the ILU apply in the solver's configuration (both plans partitioned, the intermediate kept in
     # the upper factor's order)
     s = hec.IluSolver([dev(a) for a in L], [dev(a) for a in U], vdt=vdt)
-    s.partition(dev(part), nparts, threads=1024)
+    s.partition(dev(part), nparts, threads=512)
     z = s.apply(dev(b)).cpu().numpy()
     Lr, Ur = _bounds.rounded(L, vdt), _bounds.rounded(U, vdt)
     y = oracle.lower_solve(Lr, b)
