@@ -248,10 +248,10 @@ def main():
                     help="at most this many timed oracle steps (each a whole solve) in the reference arm")
     ap.add_argument("--sweep", default="part", choices=["part", "global"],
                     help="single-RHS sweep schedule of the timed step: x-pencil partitioned (default) or global")
-    ap.add_argument("--apply-only", choices=["ilu0_16rhs", "ras64_16rhs", "stage"], default=None,
-                    help="only time the 16-right-hand-side L+U apply of this preconditioner, or one learned-stage "
-                         "application (a short run, e.g. to profile the multi-right-hand-side sweep or the "
-                         "convolution)")
+    ap.add_argument("--apply-only", choices=["ilu0_16rhs", "ras64_16rhs", "ras_pencils_1rhs", "stage"], default=None,
+                    help="only time the L+U apply of this preconditioner (16 right-hand sides, or one for RAS on "
+                         "x-pencil subdomains with partitioned sweeps), or one learned-stage application (a "
+                         "short run, e.g. to profile a sweep or the convolution)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -412,6 +412,7 @@ def main():
                     head["sweep_us"] = roofline["avg_sweep_us"]
                 head["breakdown_ms"] = line.get("breakdown_ms")
                 head["gram_schmidt"] = gram_schmidt_times(hec, torch, Ad, L, U, bd, sched)
+                head["ras_pencils"] = ras_pencil_times(hec, torch, Ad, bd, m, hbm)
         line = head
     if rank == 0 and not args.no_variants:
         line["variants"] = variants(hec, torch, Ad, L, U, bd, HA0, n, nnzL, nnzU, hbm, Schedule("part", m, devn, torch))
@@ -786,8 +787,9 @@ def run_stage_only(args):
 
 def run_apply_only(args):
     """The 16-right-hand-side L+U apply of one preconditioner (GPU ILU(0) of the whole matrix, or
-    RAS with 64 box subdomains), FP32 factor values, autotuned launch shape: W untimed and K timed
-    applies; prints one JSON line with the apply time and its algorithmic GB/s."""
+    RAS with 64 box subdomains), FP32 factor values, autotuned launch shape, or the single-RHS
+    apply of RAS on 16 x 16 x-pencil subdomains with one partitioned part per subdomain: W untimed
+    and K timed applies; prints one JSON line with the apply time and its algorithmic GB/s."""
     import torch
     from paper_1606_00541_gb300 import hec, synth
     if args.apply_only == "stage":
@@ -796,8 +798,15 @@ def run_apply_only(args):
     n = m ** 3
     A, _ = make_problem(m)
     Ad = [torch.as_tensor(a, device="cuda") for a in A]
-    B = torch.as_tensor(synth.uniform_vector(n, 500, nrhs=16), device="cuda")
-    if args.apply_only == "ras64_16rhs":
+    k = 1 if args.apply_only == "ras_pencils_1rhs" else 16
+    B = torch.as_tensor(synth.uniform_vector(n, 500, nrhs=k), device="cuda")
+    if args.apply_only == "ras_pencils_1rhs":
+        part, ns = synth.grid_boxes(m, RAS_PENCILS)
+        s = hec.RasSolver(Ad, torch.as_tensor(part, device="cuda"), ns, vdt="f32")
+        sp, nsp = subdomain_parts(s.ext_ptr.cpu().numpy())
+        s.partition(torch.as_tensor(sp, device="cuda"), nsp, threads=part_threads(m))
+        nnzl, nnzu = int(s.L[1].numel()), int(s.U[1].numel())
+    elif args.apply_only == "ras64_16rhs":
         part, ns = synth.box_partition(m, ras_cuts(m))
         s = hec.RasSolver(Ad, torch.as_tensor(part, device="cuda"), ns, vdt="f32", max_nrhs=16)
         nnzl, nnzu = int(s.L[1].numel()), int(s.U[1].numel())
@@ -806,7 +815,7 @@ def run_apply_only(args):
         L, U = Lh.tensors(), Uh.tensors()
         s = hec.IluSolver(L, U, vdt="f32", max_nrhs=16)
         nnzl, nnzu = int(L[1].numel()), int(U[1].numel())
-    shapes = s.autotune(16)
+    shapes = s.autotune(16) if k == 16 else "x-pencil subdomains, %d threads a part" % part_threads(m)
     for _ in range(args.warmup):
         s.apply(B)
     torch.cuda.synchronize()
@@ -818,11 +827,69 @@ def run_apply_only(args):
     torch.cuda.synchronize()
     ta = e0.elapsed_time(e1) / 1000.0 / args.steps
     nl = s.HL.info().n
-    Bytes = sweep_bytes(nnzl, nl, 16, 4) + sweep_bytes(nnzu, nl, 16, 4)
+    Bytes = sweep_bytes(nnzl, nl, k, 4) + sweep_bytes(nnzu, nl, k, 4)
     hbm, src = peaks()
     print(json.dumps({"apply": args.apply_only, "rows": nl, "levels_L": s.lvL.nlev, "levels_U": s.lvU.nlev,
                       "lu_apply_us": ta * 1e6, "bytes": Bytes, "lu_gbs": Bytes / ta / 1e9,
                       "frac_hbm": Bytes / ta / 1e9 / hbm, "launch_shape": shapes}), flush=True)
+
+
+RAS_PENCILS = (1, 16, 16)
+
+
+def subdomain_parts(ext_ptr):
+    """Part vector over the extended rows of a RAS system that makes every subdomain one part of
+    the partitioned sweep (the block-diagonal factors have no dependency between subdomains, so
+    no chain crosses a part)."""
+    sizes = np.diff(np.asarray(ext_ptr, dtype=np.int64))
+    return np.repeat(np.arange(len(sizes), dtype=np.int32), sizes), len(sizes)
+
+
+def ras_pencil_times(hec, torch, Ad, bd, m, hbm, vdts=("f64", "f32")):
+    """RAS (Sec. 3, Eq. 4) with the m^3 grid cut into 16 x 16 x-pencil subdomains (overlap 1), one
+    resident 512-thread part per subdomain, single right-hand side b of the main workload: set-up
+    (GPU extension, ILU(0) of every block, analysis, packing, partitioned layout) and
+    FGMRES(30) to 1e-8 with plain FP64 and mixed FP32 factor values, and the L+U apply."""
+    from paper_1606_00541_gb300 import synth
+    dev = Ad[0].device
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    part, ns = synth.grid_boxes(m, RAS_PENCILS)
+    out = {"subdomains": ns, "overlap": 1, "threads_per_part": part_threads(m)}
+    for vdt in vdts:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = hec.RasSolver(Ad, torch.as_tensor(part, device=dev), ns, vdt=vdt)
+        sp, nsp = subdomain_parts(s.ext_ptr.cpu().numpy())
+        s.partition(torch.as_tensor(sp, device=dev), nsp, threads=part_threads(m))
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        s.solve(bd, restart=RESTART, rtol=RTOL, max_iters=5000)
+        torch.cuda.synchronize()
+        e0.record()
+        _, info = s.solve(bd, restart=RESTART, rtol=RTOL, max_iters=5000)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1000.0
+        r = torch.zeros(bd.shape[0], dtype=torch.float64, device=dev)
+        r.copy_(bd)
+        for _ in range(3):
+            s.apply(r)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(10):
+            s.apply(r)
+        e1.record()
+        torch.cuda.synchronize()
+        ta = e0.elapsed_time(e1) / 1000.0 / 10
+        sv = {"f64": 8, "f32": 4, "bf16": 2}[vdt]
+        nl, nu = s.HL.info(), s.HU.info()
+        B = sweep_bytes(int(s.L[1].numel()), nl.n, 1, sv) + sweep_bytes(int(s.U[1].numel()), nu.n, 1, sv)
+        out[vdt] = {"time_to_1e-8_s": t, "iterations": info["iterations"], "converged": info["converged"],
+                    "true_rel_residual": info["rel_residual"], "setup_s": setup_s, "rows": nl.n,
+                    "levels_L": s.lvL.nlev, "levels_U": s.lvU.nlev, "lu_apply_us": ta * 1e6,
+                    "lu_gbs": B / ta / 1e9, "frac_hbm": B / ta / 1e9 / hbm}
+        del s
+    return out
 
 
 def batched_variants(hec, torch, Ad, L, U, n, hbm):

@@ -214,6 +214,25 @@ def test_cfg3_ras64_16_rhs(hec):
         assert relmax(Z[:, q], oracle.ras_apply(Ro, R[:, q])) <= 1e-11
 
 
+def test_ras_pencils_one_part_per_subdomain(hec):
+    """The bench's RAS form at 128^3: 16 x 16 x-pencil subdomains (overlap 1), every subdomain one
+    512-thread part of the partitioned sweeps, GPU ILU(0) of the blocks and FP64 values, against
+    the oracle's RAS apply (Eq. 4) with its own factors."""
+    m = 128
+    A = synth.fv7_lognormal(m, sigma=2.0, seed=0)
+    part, ns = synth.grid_boxes(m, (1, 16, 16))
+    Ro = oracle.ras_setup(A, part, ns)
+    s = hec.RasSolver([dev(a) for a in A], dev(part), ns, vdt="f64")
+    assert np.array_equal(s.ext_ptr.cpu().numpy(), Ro["ext_ptr"])
+    sp = np.repeat(np.arange(ns, dtype=np.int32), np.diff(Ro["ext_ptr"]))
+    s.partition(dev(sp), ns, threads=512)
+    assert s.lvL.nlev < 160 and s.lvU.nlev < 160  # one pencil's levels, not the grid's 382
+    r = synth.uniform_vector(m ** 3, 19)
+    for _ in range(2):
+        z = s.apply(dev(r)).cpu().numpy()
+        assert relmax(z, oracle.ras_apply(Ro, r)) <= 1e-11
+
+
 def test_cfg4_200cubed_levels_and_sweeps(hec):
     m = 200
     A = synth.fv7_lognormal(m, sigma=2.0, seed=0)

@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 import torch
 
+import _bounds
 import oracle
 from paper_1606_00541_gb300 import synth
 
@@ -177,3 +178,47 @@ def test_ras_setup_rejects_other_overlaps(hec):
     part, ns = synth.box_partition(6, [3, 3])
     with pytest.raises(Exception):
         hec.ras_setup(*[dev(a) for a in A], dev(part), ns, overlap=2)
+
+
+@pytest.mark.parametrize("vdt", ["f64", "f32"])
+def test_ras_one_part_per_subdomain(hec, vdt):
+    """RAS on x-pencil subdomains, every subdomain one part of the partitioned sweeps: the blocks of
+    Eq. 4 are independent, so no dependency crosses a part.  The apply equals the unpartitioned
+    apply up to summation order, and a second apply (the other of the double-buffered solution
+    words) repeats the first bit for bit; with the
+    oracle's FP64 factors it matches the oracle's RAS apply to 1e-12 (FP64 values) or, with FP32
+    values, the oracle's apply on the same rounded values within the FP32 substitution error; the
+    partitioned solve reaches 1e-8 in the oracle's iteration count."""
+    m = 16
+    A = synth.fv7_lognormal(m, seed=5)
+    n = m ** 3
+    part, ns = synth.grid_boxes(m, (1, 4, 4))
+    Ro = oracle.ras_setup(A, part, ns)
+    s = hec.RasSolver([dev(a) for a in A], dev(part), ns, vdt=vdt,
+                      factors=([dev(a) for a in Ro["L"]], [dev(a) for a in Ro["U"]]))
+    r = synth.uniform_vector(n, 17)
+    ref = s.apply(dev(r)).cpu().numpy()
+    sizes = np.diff(s.ext_ptr.cpu().numpy())
+    sp = np.repeat(np.arange(ns, dtype=np.int32), sizes)
+    assert s.partition(dev(sp), ns, threads=512) == ns
+    got = s.apply(dev(r)).cpu().numpy()
+    assert relmax(got, ref) <= (1e-12 if vdt == "f64" else 1e-5)
+    assert np.array_equal(s.apply(dev(r)).cpu().numpy(), got)
+    if vdt == "f64":
+        assert relmax(got, oracle.ras_apply(Ro, r)) <= 1e-12
+    else:
+        # the block-diagonal apply on the extended rows with the stored (rounded) values, restricted
+        # to the owned rows, under the componentwise FP32 substitution bound
+        Lr, Ur = _bounds.rounded(Ro["L"], "f32"), _bounds.rounded(Ro["U"], "f32")
+        idx = Ro["ext_idx"]
+        y = oracle.lower_solve(Lr, r[idx])
+        z = oracle.upper_solve(Ur, y)
+        bound = _bounds.apply_bound(Lr, Ur, y, z)
+        own = part[idx] == np.repeat(np.arange(ns), np.diff(Ro["ext_ptr"]))
+        assert np.count_nonzero(own) == n
+        assert np.all(np.abs(got[idx[own]] - z[own]) <= bound[own])
+    b = synth.uniform_vector(n, 18)
+    x, info = s.solve(dev(b), rtol=1e-8)
+    ref_its = oracle.fgmres(A, b, ("ras", Ro), m=30, rtol=1e-8)["iters"]
+    assert info["converged"] and info["rel_residual"] <= 1e-8
+    assert abs(info["iterations"] - ref_its) <= (1 if vdt == "f64" else 2)
