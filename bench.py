@@ -788,7 +788,7 @@ def run_stage_only(args):
 def run_apply_only(args):
     """The 16-right-hand-side L+U apply of one preconditioner (GPU ILU(0) of the whole matrix, or
     RAS with 64 box subdomains), FP32 factor values, autotuned launch shape, or the single-RHS
-    apply of RAS on 16 x 16 x-pencil subdomains with one partitioned part per subdomain: W untimed
+    apply of RAS on box subdomains (ras_pencil_grid) with one partitioned part per subdomain: W untimed
     and K timed applies; prints one JSON line with the apply time and its algorithmic GB/s."""
     import torch
     from paper_1606_00541_gb300 import hec, synth
@@ -801,10 +801,11 @@ def run_apply_only(args):
     k = 1 if args.apply_only == "ras_pencils_1rhs" else 16
     B = torch.as_tensor(synth.uniform_vector(n, 500, nrhs=k), device="cuda")
     if args.apply_only == "ras_pencils_1rhs":
-        part, ns = synth.grid_boxes(m, RAS_PENCILS)
+        nb, threads = ras_pencil_grid(m)
+        part, ns = synth.grid_boxes(m, nb)
         s = hec.RasSolver(Ad, torch.as_tensor(part, device="cuda"), ns, vdt="f32")
         sp, nsp = subdomain_parts(s.ext_ptr.cpu().numpy())
-        s.partition(torch.as_tensor(sp, device="cuda"), nsp, threads=part_threads(m))
+        s.partition(torch.as_tensor(sp, device="cuda"), nsp, threads=threads)
         nnzl, nnzu = int(s.L[1].numel()), int(s.U[1].numel())
     elif args.apply_only == "ras64_16rhs":
         part, ns = synth.box_partition(m, ras_cuts(m))
@@ -815,7 +816,7 @@ def run_apply_only(args):
         L, U = Lh.tensors(), Uh.tensors()
         s = hec.IluSolver(L, U, vdt="f32", max_nrhs=16)
         nnzl, nnzu = int(L[1].numel()), int(U[1].numel())
-    shapes = s.autotune(16) if k == 16 else "x-pencil subdomains, %d threads a part" % part_threads(m)
+    shapes = s.autotune(16) if k == 16 else "%s box subdomains, %d threads a part" % ras_pencil_grid(m)
     for _ in range(args.warmup):
         s.apply(B)
     torch.cuda.synchronize()
@@ -834,7 +835,17 @@ def run_apply_only(args):
                       "frac_hbm": Bytes / ta / 1e9 / hbm, "launch_shape": shapes}), flush=True)
 
 
-RAS_PENCILS = (1, 16, 16)
+def ras_pencil_grid(m):
+    """Subdomain boxes per axis and threads a part of the RAS form with one partitioned part per
+    subdomain, or None where the extended solution cannot stay in the SMs' shared memory.  On
+    128^3, 4 x 12 x 12 boxes of 32 x 10..11 x 10..11 cells (576 subdomains, 54 levels a factor,
+    four 256-thread parts an SM).  Measured there, FP32 values, FGMRES(30) to 1e-8 (iterations,
+    levels a factor): 4 x 12 x 12 / 256 threads 51.0 ms (148, 54); 2 x 8 x 19 / 512 52.5 ms
+    (149, 87); 2 x 12 x 12 / 512 52.6 ms (147, 86); 3 x 12 x 12 / 256 52.9 ms (148, 65);
+    2 x 16 x 16 / 256 56.8 ms (157, 80); 1 x 12 x 12 / 1024 58.3 ms (148, 150); 1 x 16 x 16 / 512
+    61.0 ms (155, 144); 1 x 20 x 20 / 256 63.4 ms (149, 142); 1 x 16 x 16 without overlap (block
+    ILU) 83.7 ms (225, 142)."""
+    return ((4, 12, 12), 256) if m <= 160 else None
 
 
 def subdomain_parts(ext_ptr):
@@ -846,21 +857,25 @@ def subdomain_parts(ext_ptr):
 
 
 def ras_pencil_times(hec, torch, Ad, bd, m, hbm, vdts=("f64", "f32")):
-    """RAS (Sec. 3, Eq. 4) with the m^3 grid cut into 16 x 16 x-pencil subdomains (overlap 1), one
-    resident 512-thread part per subdomain, single right-hand side b of the main workload: set-up
+    """RAS (Sec. 3, Eq. 4) with the m^3 grid cut into box subdomains (ras_pencil_grid, overlap 1),
+    one resident part per subdomain, single right-hand side b of the main workload: set-up
     (GPU extension, ILU(0) of every block, analysis, packing, partitioned layout) and
     FGMRES(30) to 1e-8 with plain FP64 and mixed FP32 factor values, and the L+U apply."""
     from paper_1606_00541_gb300 import synth
+    grid = ras_pencil_grid(m)
+    if grid is None:
+        return {"skipped": "the extended solution of %d^3 does not fit in the SMs' shared memory" % m}
+    nb, threads = grid
     dev = Ad[0].device
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    part, ns = synth.grid_boxes(m, RAS_PENCILS)
-    out = {"subdomains": ns, "overlap": 1, "threads_per_part": part_threads(m)}
+    part, ns = synth.grid_boxes(m, nb)
+    out = {"subdomains": ns, "boxes": list(nb), "overlap": 1, "threads_per_part": threads}
     for vdt in vdts:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s = hec.RasSolver(Ad, torch.as_tensor(part, device=dev), ns, vdt=vdt)
         sp, nsp = subdomain_parts(s.ext_ptr.cpu().numpy())
-        s.partition(torch.as_tensor(sp, device=dev), nsp, threads=part_threads(m))
+        s.partition(torch.as_tensor(sp, device=dev), nsp, threads=threads)
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
         s.solve(bd, restart=RESTART, rtol=RTOL, max_iters=5000)

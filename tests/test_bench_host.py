@@ -64,3 +64,18 @@ def test_recorded_traffic_follows_the_source_digest(monkeypatch, tmp_path):
     assert bench.recorded_traffic("global") is None  # no capture
     monkeypatch.setattr(bench, "sweep_source_digest", lambda: "0" * 16)
     assert bench.recorded_traffic("part") is None  # sources changed since the capture
+
+
+def test_ras_pencil_grid_parts_fit():
+    """The RAS form's subdomains, one partitioned part each, are all resident: the parts an SM
+    needs fit its 64K registers at 60 a thread and its 228 KB of shared memory with FP64
+    solutions (1 KB reserved a block); grids whose extended solution cannot fit are skipped."""
+    from paper_1606_00541_gb300 import synth
+    nb, threads = bench.ras_pencil_grid(128)
+    A = synth.fv7_lognormal(128)
+    part, ns = synth.grid_boxes(128, nb)
+    ptr, _ = oracle.ras_extend(A, part, ns)
+    per_sm = -(-ns // 152)
+    assert per_sm * threads * 60 <= 65536
+    assert per_sm * (int(np.diff(ptr).max()) * 8 + 1024) <= 228 * 1024
+    assert bench.ras_pencil_grid(200) is None
