@@ -79,3 +79,20 @@ def test_ras_pencil_grid_parts_fit():
     assert per_sm * threads * 60 <= 65536
     assert per_sm * (int(np.diff(ptr).max()) * 8 + 1024) <= 228 * 1024
     assert bench.ras_pencil_grid(200) is None
+
+
+def test_subdomain_parts_have_no_crossing_dependency():
+    """Eq. 4: the RAS factors are block diagonal over the extended subdomains, so the part vector
+    of bench.subdomain_parts (the subdomain of each extended row) puts both ends of every factor
+    entry in the same part; the parts cover the extended rows in order."""
+    from paper_1606_00541_gb300 import synth
+    m = 12
+    A = synth.fv7_lognormal(m, seed=4)
+    part, ns = synth.grid_boxes(m, (2, 3, 3))
+    R = oracle.ras_setup(A, part, ns)
+    sp, nsp = bench.subdomain_parts(R["ext_ptr"])
+    assert nsp == ns and len(sp) == R["ext_ptr"][-1]
+    assert np.all(np.diff(sp) >= 0) and np.array_equal(np.bincount(sp, minlength=ns), np.diff(R["ext_ptr"]))
+    for rp, ci, _ in (R["L"], R["U"]):
+        rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+        assert np.array_equal(sp[rows], sp[ci])
