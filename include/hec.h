@@ -211,18 +211,24 @@ hec_status sptrsv_upper(const sptrsv_plan* p, int nrhs, const double* b, int ldb
                         int ldx, void* stream);
 
 /* Partitioned sweep (a GB300 schedule of Alg. 2's level loop, same results up to summation
- * order): the rows are split into nparts parts, one thread block per part (all resident, so
- * nparts <= sptrsv_partition_capacity()).  A block takes its rows level by level in the global
- * level order with a block barrier between its levels; a dependency on a row of the same part
- * is then a plain load, and only dependencies on other parts wait point to point through L2.
- * part: device int[n], the part of each ORIGINAL row (compact regions of the grid work best; the
- * paper partitions with METIS), or NULL for contiguous ranges of the original row index.
- * threads: 128, 256, 512 or 1024 (0 = 256) per block; the part's level is worked by all the
- * block's warps, so large parts want 1024.  Applies to single-right-hand-side sweeps of this
- * plan (sptrsv_lower / sptrsv_upper / ilu_apply with nrhs = 1); nparts = 0 removes it.  The plan
- * keeps its own copy of the factor in the partitioned order and, for FP32 or BF16 values, an
- * n-entry buffer into which each sweep first gathers its right-hand side in that order.
- * Synchronizes `stream`. */
+ * order): the rows are split into nparts parts, one resident thread block per part (cooperative
+ * launch, so nparts <= sptrsv_partition_capacity()).  Inside a part the rows keep the global
+ * level order, cut into level-aligned chunks of at most 32 rows dealt round-robin to the block's
+ * warps; each row waits point to point for exactly its dependencies.  The part's solution lives
+ * in shared memory (the value is its own flag), so a dependency on a row of the same part is an
+ * SM-local poll, and only a dependency on another part polls the global solution through L2.
+ * part: device int[n], the part of each row of the plan's factor in its ORIGINAL numbering (for
+ * a RAS preconditioner, the extended rows; compact regions of the grid work best, and with one
+ * part per RAS subdomain no dependency crosses a part, since the factors are block diagonal;
+ * the paper partitions with METIS), or NULL for contiguous ranges of the row index.
+ * threads: 128, 256, 512 or 1024 (0 = 256) per block.  Fails with INVALID_ARG when the parts
+ * cannot all be resident at that block size, or when the largest part's solution (FP64 values:
+ * 8 bytes a row, else 4) leaves room for fewer resident blocks than nparts.  Applies to single-
+ * right-hand-side sweeps of this plan (sptrsv_lower / sptrsv_upper / ilu_apply with nrhs = 1);
+ * nparts = 0 removes it.  The plan keeps its own copy of the factor in the partitioned order,
+ * two plan-order solution buffers (a sweep polls one and resets the other for the next sweep),
+ * and, for FP32 or BF16 values, an n-entry buffer into which the lower sweep of an ilu_apply
+ * gathers its right-hand side in that order.  Synchronizes `stream`. */
 hec_status sptrsv_plan_partition(sptrsv_plan* p, const int* part, int nparts, int threads,
                                  void* stream);
 int sptrsv_partition_capacity(const sptrsv_plan* p, int threads);
