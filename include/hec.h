@@ -227,8 +227,9 @@ hec_status sptrsv_upper(const sptrsv_plan* p, int nrhs, const double* b, int ldb
  * right-hand-side sweeps of this plan (sptrsv_lower / sptrsv_upper / ilu_apply with nrhs = 1);
  * nparts = 0 removes it.  The plan keeps its own copy of the factor in the partitioned order,
  * two plan-order solution buffers (a sweep polls one and resets the other for the next sweep),
- * and, for FP32 or BF16 values, an n-entry buffer into which the lower sweep of an ilu_apply
- * gathers its right-hand side in that order.  Synchronizes `stream`. */
+ * and, for FP32 or BF16 values, an n-entry buffer into which each sweep first gathers its part's
+ * rows of the right-hand side in that order (the upper sweep of an ilu_apply receives y already
+ * in that order and skips it).  Synchronizes `stream`. */
 hec_status sptrsv_plan_partition(sptrsv_plan* p, const int* part, int nparts, int threads,
                                  void* stream);
 int sptrsv_partition_capacity(const sptrsv_plan* p, int threads);
