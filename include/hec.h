@@ -524,7 +524,7 @@ hec_status hec_ras_destroy(hec_ras* R);
  * allocation is forbidden, or they cannot afford a cudaMalloc (which may synchronize the
  * device) inside a latency-critical loop.  This call allocates nothing: the scratch it needs
  * (chunk table, level-ordered solution, status word) lives in one static device buffer of
- * sptrsv_noalloc_capacity() bytes (32 MiB), which every GPU that loads the library holds until
+ * sptrsv_noalloc_capacity() bytes (32 MiB), which a device holds from the first call on it until
  * the process exits.  The caller still passes tri and lv (built once with sptrsv_analyze and
  * hec_from_csr) and the device arrays b and x, with the layout of sptrsv_lower.  The lane
  * layout is that of a plan with default settings (for one right-hand side the lanes-per-row rule
