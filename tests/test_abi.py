@@ -69,3 +69,16 @@ def test_invalid_arguments_rejected_on_host(lib):
     lib.fgmres_solve.restype = ctypes.c_int
     st = lib.fgmres_solve(None, None, 1, None, 1, None, 1, 30, ctypes.c_double(1e-8), 10, None, None)
     assert st == 1
+
+
+def test_binding_fails_loudly_without_the_library():
+    """The Python binding has no CPU fallback: loaded from a place without libhec.so it raises
+    ImportError instead of defining the calls."""
+    import types
+    src_path = os.path.join(ROOT, "paper_1606_00541_gb300", "hec.py")
+    mod = types.ModuleType("hec_without_library")
+    mod.__file__ = os.path.join(ROOT, "no_such_directory", "hec.py")
+    with pytest.raises(ImportError, match="libhec.so is not built"):
+        exec(compile(open(src_path).read(), mod.__file__, "exec"), mod.__dict__)
+    assert "ilu_apply" not in mod.__dict__
+
