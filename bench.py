@@ -41,6 +41,14 @@ def workload_name(m):
             "FGMRES(%d) FP64 to %.0e" % (m, m ** 3, RESTART, RTOL))
 
 
+def workload_config(m, nnz_a, nnz_l, nnz_u, world):
+    """The `config` object of the JSON line; both arms run the same workload and print the same
+    object (the factors' patterns are the same on both sides: ILU(0) of the same matrix)."""
+    return {"workload": workload_name(m), "n": m ** 3, "nnz_A": int(nnz_a), "nnz_L": int(nnz_l),
+            "nnz_U": int(nnz_u), "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs larger than L2 (about 1 GB working set)"}
+
+
 def make_problem(m, seed=0):
     from paper_1606_00541_gb300 import synth
     A = synth.fv7_lognormal(m, sigma=2.0, seed=seed)
@@ -202,7 +210,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": v, "unit": "solves/s", "impl": "reference", "n_gpus": args.gpus,
             "steps": steps, "warmup": warm, "ms_per_step": 1000.0 * total / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(m), "l2": "inputs larger than L2"},
+            "config": workload_config(m, A[0][-1], len(L[1]), len(U[1]), args.gpus),
             "fgmres_iterations": its[-1], "converged": all(conv),
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
                              "sample": "serial C oracle, one host core: %d whole steps, each level analysis + HEC "
@@ -369,9 +377,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * step_s, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": workload_name(m), "n": n, "nnz_A": int(A[0][-1]), "nnz_L": nnzL, "nnz_U": nnzU,
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (about 1 GB working set)"},
+            "config": workload_config(m, A[0][-1], nnzL, nnzU, world),
             "fgmres_iterations": its, "true_rel_residual": relres, "factor_s": factor_s,
             "sweep_schedule": sched.describe(),
             "roofline": roofline,
