@@ -252,8 +252,9 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cfg4", action="store_true", help="also run the 200^3 learned-stage comparison")
-    ap.add_argument("--ref-max-steps", type=int, default=3,
-                    help="at most this many timed oracle steps (each a whole solve) in the reference arm")
+    ap.add_argument("--ref-max-steps", type=int, default=20,
+                    help="at most this many timed oracle steps (each a whole solve, about 11 s on one Grace "
+                         "core) in the reference arm")
     ap.add_argument("--sweep", default="part", choices=["part", "global"],
                     help="single-RHS sweep schedule of the timed step: x-pencil partitioned (default) or global")
     ap.add_argument("--apply-only", choices=["ilu0_16rhs", "ras64_16rhs", "ras_pencils_1rhs", "stage"], default=None,
