@@ -195,7 +195,7 @@ def run_reference(args):
     # every step is a whole solve to 1e-8 (several seconds on one core), so the count of timed
     # steps is capped to keep the run within a few minutes; the line reports the count run
     steps = max(1, min(args.steps, args.ref_max_steps))
-    warm = max(1, min(args.warmup, 3))
+    warm = max(1, args.warmup)  # each warm-up is short: set-up and two iterations
     for _ in range(warm):
         oracle_warm(A, b, L, U)
     times, its, conv, setups = [], [], [], []
